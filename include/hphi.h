@@ -1,0 +1,249 @@
+/*
+ * hphi.h -- C ABI of the GB300 (sm_103a) library for the matrix-free
+ * Hamiltonian-vector product of spin-1/2 and Hubbard models and the Krylov /
+ * thermal-pure-quantum drivers built on it.
+ *
+ * What the library computes (arXiv 2307.13222, "Update of H-Phi"):
+ *   - every iterative method of the paper reduces to repeated products of the
+ *     Hamiltonian with a wave function (Sec. 1; Sec. 3.4; Sec. 3.5.1), done
+ *     here matrix-free over a bit-encoded basis;
+ *   - Lanczos ground states (Sec. 1, Table 1), canonical TPQ steps
+ *     (Sec. 3.5.1, the equations of U_c and beta_k), and the vector kernels
+ *     around them.
+ * Hamiltonians (Sec. 3.1.1 Heisenberg example; Sec. 3.4 equation of
+ * H_quench; Sec. 5 Eq. ham_general):
+ *   spin-1/2  H = sum_b [ Jz_b S^z_i S^z_j + Jxy_b (S^x_i S^x_j + S^y_i S^y_j) ]
+ *   Hubbard   H = - sum t (c^+_{i s} c_{j s} + h.c.) + U sum_i n_{i up} n_{i dn}
+ *                 + sum V n_i n_j
+ * Basis (the paper leaves it to its version-1 predecessor): bit i of a spin
+ * string is site i (1 = up spin / occupied); sector states are in ascending
+ * integer order and ranked with H. Q. Lin's two-table index
+ *   rank(s) = ja[s & (2^N_lo - 1)] + jb[s >> N_lo],  N_lo = N - floor(N/2);
+ * a Hubbard row is rank_up * D_dn + rank_dn, and a fermion state is
+ *   prod_{i asc} c^+_{i up} prod_{i asc} c^+_{i dn} |0>, so a hop of species s
+ *   between i and j carries (-1)^(# s-fermions strictly between i and j).
+ *
+ * Conventions for every call:
+ *   - Status: 0 on success, a negative HPHI_E_* code otherwise; the message is
+ *     in hphi_last_error(ctx).  No call aborts the process or throws.
+ *   - Device vectors are caller-owned raw device pointers, row-major
+ *     [D][nvec] with leading dimension ld (elements, >= nvec).  Complex
+ *     dtypes store (re, im) pairs; ld counts complex elements.  The library
+ *     never frees or keeps them after the call returns.
+ *   - Host arrays (double *... "host") are caller-owned host memory.
+ *   - Work is enqueued on the context's stream.  Calls that return host
+ *     scalars (dot, nrm2, drivers) synchronise that stream before returning;
+ *     hphi_apply_H, hphi_axpy, hphi_scal and hphi_random_vector are
+ *     asynchronous.
+ *   - Handles (ctx, basis, ham) are library-owned; destroy them with the
+ *     matching call.  A basis or ham belongs to the device of the context it
+ *     was built with.  A context is not thread-safe.
+ */
+#ifndef HPHI_H
+#define HPHI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HPHI_API __attribute__((visibility("default")))
+#else
+#define HPHI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HPHI_OK 0
+#define HPHI_E_INVAL (-1)        /* bad argument, size, alias or term        */
+#define HPHI_E_NOMEM (-2)        /* device or host allocation failed         */
+#define HPHI_E_CUDA (-3)         /* a CUDA runtime error (text in last_error) */
+#define HPHI_E_NOTCONV (-4)      /* driver hit max_steps before tolerance    */
+#define HPHI_E_NUMERIC (-5)      /* NaN/Inf or a non-positive norm           */
+#define HPHI_E_DEVICE_CHECK (-6) /* a device-side consistency check failed   */
+#define HPHI_E_TIMEOUT (-7)      /* a bounded device-side wait ran out       */
+
+/* ---- models (Table 1 of the paper: Spin, SpinGC, Hubbard) --------------- */
+#define HPHI_SPIN_HALF 0    /* spin-1/2, fixed number of up spins (S^z)     */
+#define HPHI_SPIN_HALF_GC 1 /* spin-1/2, full 2^N space                     */
+#define HPHI_HUBBARD 2      /* Hubbard, fixed N_up and N_dn                  */
+
+/* ---- vector element types ----------------------------------------------- */
+#define HPHI_F64 0
+#define HPHI_F32 1
+#define HPHI_C128 2 /* complex double, (re, im) pairs */
+#define HPHI_C64 3  /* complex float,  (re, im) pairs */
+
+/* ---- interaction terms (the paper's J / t / U / V terms) ----------------- */
+#define HPHI_EXCHANGE 0  /* J S_i.S_j;                 v0 = J                 */
+#define HPHI_XXZ 1       /* Jz SzSz + Jxy (SxSx+SySy);  v0 = Jz, v1 = Jxy      */
+#define HPHI_HOP 2       /* -t (c+_{is} c_{js} + h.c.); v0 = t, spin 0 up,
+                            1 down, -1 both                                  */
+#define HPHI_HUBBARD_U 3 /* U n_{i up} n_{i dn};        v0 = U, j ignored      */
+#define HPHI_DENS_DENS 4 /* V n_i n_j (n = n_up + n_dn); v0 = V               */
+
+typedef struct hphi_term {
+    int32_t kind, i, j, spin;
+    double v0, v1;
+} hphi_term;
+
+typedef struct hphi_ctx hphi_ctx;
+typedef struct hphi_basis hphi_basis;
+typedef struct hphi_ham hphi_ham;
+
+/* ---- context -------------------------------------------------------------
+ * hphi_ctx_create: binds `device` and the CUDA stream `stream` (a
+ * cudaStream_t, NULL = legacy default stream).  Errors: HPHI_E_INVAL (bad
+ * device), HPHI_E_CUDA, HPHI_E_NOMEM.  The library allocates its own
+ * workspace (reduction partials, driver vectors) lazily on the device. */
+HPHI_API int hphi_ctx_create(int device, void *stream, hphi_ctx **out);
+HPHI_API int hphi_ctx_set_stream(hphi_ctx *ctx, void *stream);
+HPHI_API void hphi_ctx_destroy(hphi_ctx *ctx);
+/* Message of the last failing call on this context ("" if none). */
+HPHI_API const char *hphi_last_error(const hphi_ctx *ctx);
+/* Number of SMs of the context's device (grid sizing information). */
+HPHI_API int hphi_ctx_sm_count(const hphi_ctx *ctx);
+
+/* ---- kernel timing ---------------------------------------------------------
+ * hphi_ctx_profile(ctx, 1) records a CUDA event pair on the context's stream
+ * around every launch of the H*x kernel (kind 0) and of the vector kernels
+ * (kind 1: dot/nrm2 partials, axpy/scal/lincomb); 0 stops recording.
+ * hphi_ctx_profile_read synchronises the stream and returns, for `kind`, the
+ * number of launches and their summed device time (ms) since the previous
+ * read of that kind, then resets that kind. */
+HPHI_API int hphi_ctx_profile(hphi_ctx *ctx, int enable);
+HPHI_API int hphi_ctx_profile_read(hphi_ctx *ctx, int kind, int64_t *launches, double *total_ms);
+
+/* ---- basis (Sec. 3.5.1: "x may be the set of spin positions"; Table 1
+ * sectors 2Sz / nelec) ------------------------------------------------------
+ * hphi_build_basis: builds the two-table rank of the sector on the device.
+ *   SPIN_HALF: n_sites <= 40 (tables of 2^ceil(N/2) entries), 0 <= n_up <= N.
+ *   SPIN_HALF_GC: n_sites <= 36; n_up, n_dn ignored.
+ *   HUBBARD: n_sites <= 32, 0 <= n_up, n_dn <= N, C(N, n) < 2^31 per species.
+ * Errors: HPHI_E_INVAL for sizes outside these limits or an empty sector,
+ * HPHI_E_NOMEM, HPHI_E_CUDA. */
+HPHI_API int hphi_build_basis(hphi_ctx *ctx, int model, int n_sites, int n_up, int n_dn, hphi_basis **out);
+HPHI_API void hphi_basis_destroy(hphi_basis *basis);
+HPHI_API int64_t hphi_basis_dim(const hphi_basis *basis);
+/* Sizes of the Lin tables of `species` (0: spins / up fermions, 1: down
+ * fermions): n_ja = 2^N_lo, n_jb = 2^N_hi.  GC models have no tables (0). */
+HPHI_API int hphi_basis_table_sizes(const hphi_basis *basis, int species, int64_t *n_ja, int64_t *n_jb);
+/* Copies the tables to host arrays of the sizes above (for bit-exact checks).
+ * jb holds ~0 for high halves that occur in no sector state. */
+HPHI_API int hphi_basis_export(hphi_ctx *ctx, const hphi_basis *basis, int species, uint32_t *ja_host, uint64_t *jb_host);
+/* Device: states of rows [row0, row0+n): su[k] (spin string / up string) and
+ * sd[k] (down string, Hubbard only; may be NULL otherwise). */
+HPHI_API int hphi_basis_states(hphi_ctx *ctx, const hphi_basis *basis, int64_t row0, int64_t n, uint64_t *su_dev,
+                      uint64_t *sd_dev);
+/* Device: rows of the n states (su, sd); -1 for a state outside the sector. */
+HPHI_API int hphi_basis_rank(hphi_ctx *ctx, const hphi_basis *basis, const uint64_t *su_dev, const uint64_t *sd_dev,
+                    int64_t n, int64_t *row_dev);
+
+/* ---- Hamiltonian (interaction list; Expert-mode terms, Sec. 3.4 and 5) -----
+ * Validates the terms (site bounds, i != j for pair terms, kind allowed for
+ * the model: spin models take EXCHANGE/XXZ, Hubbard takes HOP/HUBBARD_U/
+ * DENS_DENS) and builds the per-sector tables the kernels use.  Repeated pairs
+ * are summed.  Errors: HPHI_E_INVAL, HPHI_E_NOMEM, HPHI_E_CUDA.  The ham keeps
+ * a reference to `basis`, which must outlive it. */
+HPHI_API int hphi_build_hamiltonian(hphi_ctx *ctx, const hphi_basis *basis, const hphi_term *terms, int n_terms,
+                           hphi_ham **out);
+HPHI_API void hphi_ham_destroy(hphi_ham *ham);
+HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
+
+/* ---- H*x (the hot path) -------------------------------------------------
+ * y <- alpha * H x + beta * y for nvec columns (1 <= nvec <= 128 real
+ * columns; a complex column counts as two).  x and y are device arrays of
+ * `dtype`, [D][nvec] with leading dimensions ldx, ldy >= nvec.  beta == 0
+ * does not read y.  x and y must not overlap (HPHI_E_INVAL).  Asynchronous. */
+HPHI_API int hphi_apply_H(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, const void *x, int64_t ldx, void *y,
+                 int64_t ldy, double alpha, double beta);
+
+/* ---- matrix pattern (debug; the paper's Matrix Market export, Sec. 3.1.2) --
+ * Rows [row0, row1) of H: for each row the distinct columns (ascending) with
+ * the summed matrix element, the diagonal always included.  rowptr_host has
+ * row1-row0+1 entries; cols_host / vals_host hold at least *nnz_capacity
+ * entries.  On HPHI_E_INVAL because the capacity is too small, *nnz_capacity
+ * is set to the needed count.  Host outputs; small row ranges only. */
+HPHI_API int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, int64_t *rowptr_host,
+                      int64_t *cols_host, double *vals_host, int64_t *nnz_capacity);
+
+/* ---- vector kernels ---------------------------------------------------------
+ * n rows, nvec columns, leading dimensions in elements of `dtype`.
+ * Reductions are deterministic (fixed per-block partials, fixed-order sum)
+ * and accumulate in FP64 (FP32 inputs: compensated float-float per thread).
+ *   hphi_dot:  out_host[q] = <x_q|y_q> (complex: out_host[2q], [2q+1] = re, im
+ *              of sum conj(x) y)
+ *   hphi_nrm2: out_host[q] = |x_q|_2
+ *   hphi_axpy: y_q += a_q x_q  (a_host: nvec reals, or nvec (re, im) pairs)
+ *   hphi_scal: x_q *= a_q
+ *   hphi_random_vector: x[r][c] = Gaussian of Philox4x32-10 stream element
+ *              r * reals_per_row + c (reals_per_row = nvec, or 2*nvec for
+ *              complex), key = seed; Box-Muller of two 53-bit uniforms. */
+HPHI_API int hphi_dot(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const void *x, int64_t ldx, const void *y,
+             int64_t ldy, double *out_host);
+HPHI_API int hphi_nrm2(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const void *x, int64_t ldx, double *out_host);
+HPHI_API int hphi_axpy(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const double *a_host, const void *x, int64_t ldx,
+              void *y, int64_t ldy);
+HPHI_API int hphi_scal(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const double *a_host, void *x, int64_t ldx);
+HPHI_API int hphi_random_vector(hphi_ctx *ctx, int dtype, int64_t n, int nvec, uint64_t seed, void *x, int64_t ldx);
+
+/* ---- Lanczos ground state (Sec. 1, Table 1) ---------------------------------
+ * Three-term Lanczos from v0 (device, length D, dtype F64 or F32: the storage
+ * precision of the Krylov vectors; alpha/beta, the tridiagonal problem and
+ * the reductions are FP64).  Stops when the residual estimate
+ * beta_{m+1} |y_m| <= tol * max(1, |theta_0|) (tol <= 0: run max_steps), on
+ * an invariant subspace, or at max_steps.  With gs_out != NULL (device,
+ * length D, same dtype) a second pass rebuilds the Krylov vectors and returns
+ * the normalised Ritz vector, and `resid` is the explicit |H x - theta x|.
+ * alpha_host / beta_host (nullable) receive max_steps and max_steps+1
+ * values.  Returns HPHI_OK, HPHI_E_NOTCONV (tol > 0 not reached; result
+ * filled in), or an error. */
+typedef struct hphi_lanczos_opts {
+    int max_steps;
+    double tol;
+    int dtype;       /* HPHI_F64 or HPHI_F32 */
+    int check_every; /* host convergence check period in steps (>= 1) */
+} hphi_lanczos_opts;
+
+typedef struct hphi_lanczos_result {
+    double e0;        /* lowest Ritz value */
+    double resid_est; /* beta_{m+1} |y_m| */
+    double resid;     /* |H x - e0 x| (only with gs_out), else -1 */
+    int steps;
+    int breakdown; /* 1 if an invariant subspace ended the run */
+} hphi_lanczos_result;
+
+HPHI_API int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0, void *gs_out,
+                 double *alpha_host, double *beta_host, hphi_lanczos_result *result);
+
+/* ---- canonical TPQ step (Sec. 3.5.1) -----------------------------------------
+ * One step Phi_{k+1} = U_c(dtau) Phi_k, U_c = sum_{n<=nmax} (-dtau H/2)^n / n!,
+ * for nvec independent columns of V (device, dtype F64/F32/C128/C64, [D][nvec],
+ * ld >= nvec), evaluated by Horner stages W <- sigma V + (-dtau/2)/j H W,
+ * j = nmax .. 1, sigma = 1/sqrt(norm2_inout[q]).
+ * In:  norm2_inout[q] = |V_q|^2 of the stored column (<= 0: computed here).
+ * Out: e_host[q]  = <Phi_k|H|Phi_k> / <Phi_k|Phi_k>          (at beta_k)
+ *      h2_host[q] = <H Phi_k|H Phi_k> / <Phi_k|Phi_k>
+ *      logd_host[q] = log D_{k+1}, D_{k+1} = N_{k+1}/N_k (the relative squared
+ *                     norm of the paper's Norm_n.dat)
+ *      V_q <- Phi_{k+1} / |Phi_k| and norm2_inout[q] = |V_q|^2 = D_{k+1}.
+ * The library holds two workspace blocks of V's size.  1 <= nmax <= 64. */
+HPHI_API int hphi_tpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv, double dtau,
+                  int nmax, double *norm2_inout, double *e_host, double *h2_host, double *logd_host);
+
+/* ---- host utility: symmetric tridiagonal eigenproblem ------------------------
+ * All eigenvalues (ascending) of the n x n tridiagonal with diagonal a[0..n-1]
+ * and off-diagonal b[1..n-1] (b[k] couples rows k-1 and k; b[0] unused), by the
+ * implicit QL iteration with Wilkinson shifts; evecs (nullable, host n*n,
+ * row-major) receives the eigenvectors as columns, each with a non-negative
+ * first component.  This is the small problem of every Lanczos run (T_m of
+ * alpha/beta).  Host memory only; no GPU needed.  HPHI_E_NUMERIC if the
+ * iteration does not converge. */
+HPHI_API int hphi_tridiag_eigen(int n, const double *a, const double *b, double *evals, double *evecs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPHI_H */

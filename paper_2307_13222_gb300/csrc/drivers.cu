@@ -1,0 +1,478 @@
+// Drivers built on the H*x kernel: Lanczos ground state (the paper's
+// ground-state method, Sec. 1 and Table 1) and one canonical-TPQ step
+// (Sec. 3.5.1, U_c = sum_{n<=nmax} (-dtau H/2)^n / n!).
+//
+// Lanczos keeps the Krylov vectors unnormalised: v_k = w_k / beta_k with
+// beta_k = |w_k| (beta_0 = |v0|, w_0 = v0).  One step is
+//   u       = (1/beta_k) H w_k - (beta_k/beta_{k-1}) w_{k-1}     (fused H*x)
+//   alpha_k = <w_k, u> / beta_k                                  (same pass)
+//   w_{k+1} = u - (alpha_k/beta_k) w_k,  beta_{k+1}^2 = |w_{k+1}|^2
+// All scalars of the recurrence stay on the device (a one-thread kernel
+// derives the next coefficients from the reductions), so a run of steps needs
+// no host round trip; the host reads alpha/beta only at convergence checks and
+// solves the tridiagonal problem with the implicit QL method.
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hphi_internal.cuh"
+
+namespace hphi {
+
+// Symmetric tridiagonal eigenproblem by the implicit QL iteration with
+// Wilkinson shifts (Bowdler, Martin, Reinsch, Wilkinson, Numer. Math. 11
+// (1968) 293).  d[0..n-1] diagonal -> eigenvalues; e[0..n-2] off-diagonal
+// (destroyed); z (n*n, row-major, may be null) -> eigenvectors in columns.
+int tridiag_ql(int n, double *d, double *e, double *z) {
+    if (n <= 0) return HPHI_OK;
+    std::vector<double> ee(n, 0.0);
+    for (int i = 0; i + 1 < n; i++) ee[i] = e[i];
+    if (z)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) z[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int l = 0; l < n; l++) {
+        int iter = 0;
+        for (;;) {
+            int m = l;
+            for (; m < n - 1; m++) {
+                double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(ee[m]) <= DBL_EPSILON * dd) break;
+            }
+            if (m == l) break;
+            if (++iter > 200) return HPHI_E_NUMERIC;
+            double g = (d[l + 1] - d[l]) / (2.0 * ee[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + ee[l] / (g + (g >= 0.0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            bool early = false;
+            for (int i = m - 1; i >= l; i--) {
+                double f = s * ee[i], b = c * ee[i];
+                r = hypot(f, g);
+                ee[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    ee[m] = 0.0;
+                    early = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                if (z) {
+                    for (int k = 0; k < n; k++) {
+                        double t = z[k * n + i + 1];
+                        z[k * n + i + 1] = s * z[k * n + i] + c * t;
+                        z[k * n + i] = c * z[k * n + i] - s * t;
+                    }
+                }
+            }
+            if (early) continue;
+            d[l] -= p;
+            ee[l] = g;
+            ee[m] = 0.0;
+        }
+    }
+    return HPHI_OK;
+}
+
+namespace {
+
+enum LzMode { LZ_INIT = 0, LZ_PREP_A = 1, LZ_ALPHA = 2, LZ_BETA = 3 };
+
+// one thread: scalar bookkeeping of the device-side recurrence
+__global__ void k_lz(int mode, int k, const double *red, double *alpha, double *beta2, double *coefA, double *coefB,
+                     int *flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // *flag records the first step (k + 1) whose scalars were not finite; -1
+    // marks a start vector of zero norm
+    if (mode == LZ_INIT) {
+        beta2[0] = red[0];
+        if (!(red[0] > 0.0) || !isfinite(red[0])) *flag = -1;
+    } else if (mode == LZ_PREP_A) {
+        double bk = sqrt(beta2[k]);
+        coefA[0] = 1.0 / bk;
+        coefA[1] = k > 0 ? -bk / sqrt(beta2[k - 1]) : 0.0;
+    } else if (mode == LZ_ALPHA) {
+        double bk = sqrt(beta2[k]);
+        double a = red[0] / bk;
+        alpha[k] = a;
+        coefB[0] = -a / bk;  // coefficient of w_k
+        coefB[1] = 0.0;
+        coefB[2] = 1.0;      // coefficient of u
+        if (!isfinite(a) && *flag == 0) *flag = k + 1;
+    } else {
+        beta2[k + 1] = red[0];
+        if ((!(red[0] >= 0.0) || !isfinite(red[0])) && *flag == 0) *flag = k + 1;
+    }
+}
+
+struct LzBuffers {
+    double *alpha = nullptr, *beta2 = nullptr;
+};
+
+}  // namespace
+
+}  // namespace hphi
+
+using namespace hphi;
+
+extern "C" int hphi_tridiag_eigen(int n, const double *a, const double *b, double *evals, double *evecs) {
+    if (n < 1 || !a || !evals || (n > 1 && !b)) return HPHI_E_INVAL;
+    std::vector<double> d(a, a + n), e(n, 0.0);
+    for (int i = 0; i + 1 < n; i++) e[i] = b[i + 1];
+    std::vector<double> z(evecs ? (size_t)n * n : 0);
+    int st = tridiag_ql(n, d.data(), e.data(), evecs ? z.data() : nullptr);
+    if (st) return st;
+    // ascending order of eigenvalues (columns follow)
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; i++) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return d[p] < d[q]; });
+    for (int j = 0; j < n; j++) {
+        evals[j] = d[idx[j]];
+        if (evecs) {
+            double sg = z[idx[j]] < 0.0 ? -1.0 : 1.0;  // first component non-negative
+            for (int i = 0; i < n; i++) evecs[(size_t)i * n + j] = sg * z[(size_t)i * n + idx[j]];
+        }
+    }
+    return HPHI_OK;
+}
+
+extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0,
+                            void *gs_out, double *alpha_host, double *beta_host, hphi_lanczos_result *res) {
+    if (!ctx || !ham || !opts || !v0 || !res) return HPHI_E_INVAL;
+    ctx->err.clear();
+    const int dt = opts->dtype;
+    if (dt != HPHI_F64 && dt != HPHI_F32) return set_err(ctx, HPHI_E_INVAL, "Lanczos dtype must be F64 or F32");
+    const int M = opts->max_steps;
+    if (M < 1 || M > 100000) return set_err(ctx, HPHI_E_INVAL, "max_steps must be in [1, 100000]");
+    const int check = opts->check_every < 1 ? 1 : opts->check_every;
+    const int64_t D = ham->D;
+    const size_t es = real_size(dt);
+    if (ham->device != ctx->device) return set_err(ctx, HPHI_E_INVAL, "hamiltonian belongs to another device");
+    HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    int st;
+    if ((st = ensure_vecs(ctx, (size_t)D * es))) return st;
+    size_t np = hv_partials_size(ctx, ham, 1);
+    if (np < (size_t)ctx->sm_count * 8 * 2) np = (size_t)ctx->sm_count * 8 * 2;
+    if ((st = ensure_partials(ctx, np))) return st;
+    double *ab = nullptr;
+    HPHI_CUDA(ctx, cudaMalloc(&ab, sizeof(double) * (2 * (size_t)M + 4)));
+    double *alpha_d = ab, *beta2_d = ab + M + 1;
+    double *coefA = ctx->dscal + 3000, *coefB = ctx->dscal + 3008, *red = ctx->dscal + 3016;
+    void *prev = ctx->vec[0], *cur = ctx->vec[1], *u = ctx->vec[2];
+    std::vector<double> alpha_h(M + 1, 0.0), beta2_h(M + 2, 0.0), y;
+    int steps = 0, conv = 0, brk = 0;
+    double theta = 0.0, resid_est = -1.0;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ab);
+        return code;
+    };
+    HPHI_CUDA(ctx, cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+    if ((st = launch_copy(ctx, dt, D, 1, v0, 1, cur, 1))) return fail(st);
+    if ((st = launch_dot(ctx, dt, 0, D, 1, cur, 1, cur, 1, red))) return fail(st);
+    k_lz<<<1, 32, 0, ctx->stream>>>(LZ_INIT, 0, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
+
+    // eigen-solution of T_m from the host copies
+    auto solve_T = [&](int m) -> int {
+        std::vector<double> a(alpha_h.begin(), alpha_h.begin() + m), b(m, 0.0), ev(m), Z((size_t)m * m);
+        for (int j = 1; j < m; j++) b[j] = sqrt(beta2_h[j]);
+        int s2 = hphi_tridiag_eigen(m, a.data(), b.data(), ev.data(), Z.data());
+        if (s2) return s2;
+        theta = ev[0];
+        y.assign(m, 0.0);
+        for (int i = 0; i < m; i++) y[i] = Z[(size_t)i * m];
+        resid_est = sqrt(beta2_h[m]) * fabs(y[m - 1]);
+        return HPHI_OK;
+    };
+
+    for (int k = 0; k < M; k++) {
+        k_lz<<<1, 32, 0, ctx->stream>>>(LZ_PREP_A, k, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
+        HvLaunch A{};
+        A.dtype_real = dt;
+        A.ncol = 1;
+        A.x = cur;
+        A.ldx = 1;
+        A.y = u;
+        A.ldy = 1;
+        A.v = k > 0 ? prev : nullptr;
+        A.ldv = 1;
+        A.beta = 0.0;
+        A.coef_dev = coefA;
+        A.red[0] = R_XO;
+        A.partials = ctx->partials;
+        if ((st = launch_hv(ctx, ham, A)) || (st = reduce_hv(ctx, A, red))) return fail(st);
+        k_lz<<<1, 32, 0, ctx->stream>>>(LZ_ALPHA, k, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
+        LinComb B{};
+        B.real_dtype = dt;
+        B.n = D;
+        B.nr = 1;
+        B.x = cur;
+        B.ldx = 1;
+        B.y = u;
+        B.ldy = 1;
+        B.out = u;
+        B.ldo = 1;
+        B.coef_dev = coefB;
+        B.red_oo = 1;
+        B.partials = ctx->partials;
+        if ((st = launch_lincomb(ctx, B)) || (st = reduce_partials(ctx, ctx->partials, B.grid, 1, red)))
+            return fail(st);
+        k_lz<<<1, 32, 0, ctx->stream>>>(LZ_BETA, k, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
+        HPHI_CUDA(ctx, cudaGetLastError());
+        void *t = prev;
+        prev = cur;
+        cur = u;
+        u = t;
+        steps = k + 1;
+        if ((k + 1) % check == 0 || k + 1 == M) {
+            int flag = 0;
+            HPHI_CUDA(ctx, cudaMemcpyAsync(alpha_h.data(), alpha_d, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaMemcpyAsync(beta2_h.data(), beta2_d, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            if (flag == -1) return fail(set_err(ctx, HPHI_E_INVAL, "Lanczos: start vector has zero norm"));
+            // the first step at which beta vanished (an invariant subspace)
+            int mstop = k + 1;
+            double tn = 0.0;
+            for (int j = 0; j <= k; j++) {
+                double r = fabs(alpha_h[j]) + (j > 0 ? sqrt(beta2_h[j]) : 0.0) + sqrt(beta2_h[j + 1]);
+                tn = r > tn ? r : tn;
+                if (sqrt(beta2_h[j + 1]) <= 64.0 * DBL_EPSILON * tn) {
+                    mstop = j + 1;
+                    brk = 1;
+                    break;
+                }
+            }
+            // steps after a vanished beta divide by it; only a non-finite value
+            // before the breakdown is an error
+            if (flag > 0 && !(brk && mstop <= flag - 1))
+                return fail(set_err(ctx, HPHI_E_NUMERIC, "Lanczos: non-finite scalars at step %d", flag - 1));
+            if ((st = solve_T(mstop))) return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
+            steps = mstop;
+            if (brk) break;
+            if (opts->tol > 0.0 && mstop >= 2 && resid_est <= opts->tol * (fabs(theta) > 1.0 ? fabs(theta) : 1.0)) {
+                conv = 1;
+                break;
+            }
+        }
+    }
+    const int m = steps;
+    res->e0 = theta;
+    res->resid_est = resid_est;
+    res->resid = -1.0;
+    res->steps = m;
+    res->breakdown = brk;
+    if (alpha_host)
+        for (int j = 0; j < M; j++) alpha_host[j] = j < m ? alpha_h[j] : 0.0;
+    if (beta_host)
+        for (int j = 0; j <= M; j++) beta_host[j] = (j >= 1 && j <= m) ? sqrt(beta2_h[j]) : 0.0;
+
+    if (gs_out) {
+        // second pass: regenerate w_k with the stored alpha/beta (the same
+        // kernels on the same inputs reproduce the first pass bit for bit) and
+        // accumulate x = sum_k y_k v_k = sum_k (y_k / beta_k) w_k
+        HPHI_CUDA(ctx, cudaMemsetAsync(gs_out, 0, (size_t)D * es, ctx->stream));
+        prev = ctx->vec[0];
+        cur = ctx->vec[1];
+        u = ctx->vec[2];
+        if ((st = launch_copy(ctx, dt, D, 1, v0, 1, cur, 1))) return fail(st);
+        for (int k = 0; k < m; k++) {
+            double bk = sqrt(beta2_h[k]);
+            LinComb G{};
+            double ga = y[k] / bk, one = 1.0, zero = 0.0;
+            G.real_dtype = dt;
+            G.n = D;
+            G.nr = 1;
+            G.x = cur;
+            G.ldx = 1;
+            G.y = gs_out;
+            G.ldy = 1;
+            G.out = gs_out;
+            G.ldo = 1;
+            G.a_h = &ga;
+            G.b_h = &zero;
+            G.g_h = &one;
+            if ((st = launch_lincomb(ctx, G))) return fail(st);
+            if (k + 1 == m) break;
+            HvLaunch A{};
+            A.dtype_real = dt;
+            A.ncol = 1;
+            A.x = cur;
+            A.ldx = 1;
+            A.y = u;
+            A.ldy = 1;
+            A.v = k > 0 ? prev : nullptr;
+            A.ldv = 1;
+            A.alpha_s = 1.0 / bk;
+            A.gamma_s = k > 0 ? -bk / sqrt(beta2_h[k - 1]) : 0.0;
+            if ((st = launch_hv(ctx, ham, A))) return fail(st);
+            LinComb B{};
+            double ca = -alpha_h[k] / bk;
+            B.real_dtype = dt;
+            B.n = D;
+            B.nr = 1;
+            B.x = cur;
+            B.ldx = 1;
+            B.y = u;
+            B.ldy = 1;
+            B.out = u;
+            B.ldo = 1;
+            B.a_h = &ca;
+            B.b_h = &zero;
+            B.g_h = &one;
+            if ((st = launch_lincomb(ctx, B))) return fail(st);
+            void *t = prev;
+            prev = cur;
+            cur = u;
+            u = t;
+        }
+        double nrm = 0.0;
+        if ((st = hphi_nrm2(ctx, dt, D, 1, gs_out, 1, &nrm))) return fail(st);
+        if (!(nrm > 0.0)) return fail(set_err(ctx, HPHI_E_NUMERIC, "ground-state vector has zero norm"));
+        double inv = 1.0 / nrm;
+        if ((st = hphi_scal(ctx, dt, D, 1, &inv, gs_out, 1))) return fail(st);
+        // explicit residual |H x - theta x|
+        HvLaunch R{};
+        R.dtype_real = dt;
+        R.ncol = 1;
+        R.x = gs_out;
+        R.ldx = 1;
+        R.y = ctx->vec[0];
+        R.ldy = 1;
+        R.v = gs_out;
+        R.ldv = 1;
+        R.alpha_s = 1.0;
+        R.gamma_s = -theta;
+        R.red[0] = R_OO;
+        R.partials = ctx->partials;
+        if ((st = launch_hv(ctx, ham, R)) || (st = reduce_hv(ctx, R, red))) return fail(st);
+        double rr = 0.0;
+        HPHI_CUDA(ctx, cudaMemcpyAsync(&rr, red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        res->resid = sqrt(rr);
+    }
+    HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ab);
+    if (opts->tol > 0.0 && !conv && !brk)
+        return set_err(ctx, HPHI_E_NOTCONV, "Lanczos: tolerance not reached in %d steps", m);
+    return HPHI_OK;
+}
+
+extern "C" int hphi_tpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv,
+                             double dtau, int nmax, double *norm2, double *e_out, double *h2_out, double *logd_out) {
+    if (!ctx || !ham || !V || !norm2 || !e_out || !h2_out || !logd_out) return HPHI_E_INVAL;
+    ctx->err.clear();
+    if (!valid_dtype(dtype)) return set_err(ctx, HPHI_E_INVAL, "unknown dtype %d", dtype);
+    if (nmax < 1 || nmax > 64) return set_err(ctx, HPHI_E_INVAL, "nmax must be in [1, 64]");
+    const int cpl = is_complex(dtype) ? 2 : 1, nr = nvec * cpl;
+    if (nvec < 1 || nr > kMaxCols) return set_err(ctx, HPHI_E_INVAL, "1 <= real columns <= %d", kMaxCols);
+    if (ldv < nvec) return set_err(ctx, HPHI_E_INVAL, "ldv < nvec");
+    if (ham->device != ctx->device) return set_err(ctx, HPHI_E_INVAL, "hamiltonian belongs to another device");
+    HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int rd = real_of(dtype);
+    const int64_t D = ham->D;
+    const int64_t ld = ldv * cpl;
+    const size_t es = real_size(rd);
+    int st;
+    if ((st = ensure_vecs(ctx, (size_t)D * nr * es))) return st;
+    size_t np = hv_partials_size(ctx, ham, nr);
+    if ((st = ensure_partials(ctx, np))) return st;
+    // |V|^2 where not supplied
+    bool need = false;
+    for (int q = 0; q < nvec; q++) need = need || !(norm2[q] > 0.0);
+    if (need) {
+        std::vector<double> nn(nvec);
+        if ((st = hphi_nrm2(ctx, dtype, D, nvec, V, ldv, nn.data()))) return st;
+        for (int q = 0; q < nvec; q++)
+            if (!(norm2[q] > 0.0)) norm2[q] = nn[q] * nn[q];
+    }
+    std::vector<double> sig(nr), al(nr), ga(nr);
+    for (int q = 0; q < nvec; q++) {
+        if (!(norm2[q] > 0.0) || !isfinite(norm2[q]))
+            return set_err(ctx, HPHI_E_NUMERIC, "column %d has a non-positive norm", q);
+        for (int c = 0; c < cpl; c++) sig[q * cpl + c] = 1.0 / sqrt(norm2[q]);
+    }
+    void *W[2] = {ctx->vec[0], ctx->vec[1]};
+    double *red = ctx->dscal + 2048;  // [3][nr]
+    std::vector<double> first(3 * nr), last(nr);
+    const void *x = V;
+    int64_t ldx = ld;
+    for (int j = nmax; j >= 1; j--) {
+        const double cj = (-0.5 * dtau) / (double)j;
+        const bool out_v = (j == 1 && nmax > 1);
+        void *out = out_v ? V : W[j & 1];
+        int64_t ldo = out_v ? ld : nr;
+        for (int c = 0; c < nr; c++) {
+            al[c] = j == nmax ? cj * sig[c] : cj;
+            ga[c] = sig[c];
+        }
+        HvLaunch L{};
+        L.dtype_real = rd;
+        L.ncol = nr;
+        L.x = x;
+        L.ldx = ldx;
+        L.y = out;
+        L.ldy = ldo;
+        L.v = V;
+        L.ldv = ld;
+        L.alpha_h = al.data();
+        L.gamma_h = ga.data();
+        L.partials = ctx->partials;
+        if (j == nmax) {
+            L.red[0] = R_XHX;
+            L.red[1] = R_HXHX;
+            L.red[2] = R_XX;
+        } else if (j == 1) {
+            L.red[0] = R_OO;
+        }
+        if ((st = launch_hv(ctx, ham, L))) return st;
+        if (j == nmax) {
+            if ((st = reduce_hv(ctx, L, red))) return st;
+            HPHI_CUDA(ctx, cudaMemcpyAsync(first.data(), red, sizeof(double) * 3 * nr, cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+        if (j == 1 && nmax > 1) {
+            if ((st = reduce_hv(ctx, L, red))) return st;
+            HPHI_CUDA(ctx, cudaMemcpyAsync(last.data(), red, sizeof(double) * nr, cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+        x = out;
+        ldx = ldo;
+    }
+    if (nmax == 1) {
+        // the single stage wrote W[1]; copy it into V and take its norms
+        if ((st = launch_copy(ctx, rd, D, nr, W[1], nr, V, ld))) return st;
+        if ((st = launch_dot(ctx, rd, 0, D, nr, V, ld, V, ld, red))) return st;
+        HPHI_CUDA(ctx, cudaMemcpyAsync(last.data(), red, sizeof(double) * nr, cudaMemcpyDeviceToHost, ctx->stream));
+        HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    for (int q = 0; q < nvec; q++) {
+        double xhx = 0, hxhx = 0, xx = 0, oo = 0;
+        for (int c = 0; c < cpl; c++) {
+            xhx += first[0 * nr + q * cpl + c];
+            hxhx += first[1 * nr + q * cpl + c];
+            xx += first[2 * nr + q * cpl + c];
+            oo += last[q * cpl + c];
+        }
+        if (!(xx > 0.0) || !(oo > 0.0) || !isfinite(oo))
+            return set_err(ctx, HPHI_E_NUMERIC, "TPQ column %d: non-finite or zero norm", q);
+        e_out[q] = xhx / xx;
+        h2_out[q] = hxhx / xx;
+        double s2 = 1.0 / norm2[q];
+        logd_out[q] = log(oo) - log(s2 * xx);
+        norm2[q] = oo;
+    }
+    return HPHI_OK;
+}

@@ -1,0 +1,235 @@
+// Internal structures shared by the translation units of libhphi.
+//
+// Layout of the hot path.  Every model is handled as a two-level structure:
+// a row is (h, q) where h indexes a "block" of consecutive rows and q the row
+// inside it.
+//   spin sector:  h = high half of the spin string (N_hi = floor(N/2) bits),
+//                 the block holds the sector states with that high half in
+//                 ascending order, q = rank of the low half among the N_lo-bit
+//                 strings of its popcount (Lin's ja), block base = jb[h].
+//   spin GC:      h = high half, q = low half, base = h << N_lo.
+//   Hubbard:      h = rank of the up string, q = rank of the down string,
+//                 base = h * D_dn.
+// A low half (or down string) is addressed by its "class position"
+// cp = cp0(h) + q, which indexes the per-low-half tables built once per
+// Hamiltonian: the diagonal part that depends on the low half only, the
+// low-low off-diagonal neighbours (ELL lists of target q' and coefficient
+// index), and for spin models the rank of the low half with one bit flipped.
+// Everything that depends on h only (high-high / up-hop neighbours as row
+// offsets, the high-only diagonal part, byte tables of the mixed diagonal
+// part) is prepared per block in shared memory by the thread block that owns
+// the block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hphi.h"
+
+namespace hphi {
+
+constexpr int kMaxHH = 128;     // high-high / up-hop neighbours of one block
+constexpr int kMaxLH = 64;      // mixed (low-high) spin bonds
+constexpr int kMaxGroups = 4;   // byte groups of the low half (<= 32 bits)
+constexpr int kMaxCoef = 512;   // coefficient table (ELL coefficient indices)
+constexpr int kMaxBond = 256;   // bonds per class in the descriptor
+constexpr int kMaxCols = 128;   // real columns of one H*x launch
+constexpr int kThreads = 256;   // threads per block of the H*x kernel
+
+enum Model { kSpin = HPHI_SPIN_HALF, kSpinGC = HPHI_SPIN_HALF_GC, kHubbard = HPHI_HUBBARD };
+
+// reductions a fused H*x launch can produce, per real column
+enum Red { R_NONE = 0, R_XHX = 1, R_HXHX = 2, R_XX = 3, R_XO = 4, R_OO = 5 };
+
+struct HHBond {   // spin bond with both sites in the high half
+    int i, j;     // bit positions inside h
+    double cz;    // -Jz/2: diagonal change when the two spins differ
+    double cxy;   // Jxy/2: off-diagonal element
+};
+struct LHBond {   // spin bond between high bit a and low bit b
+    int a, b, bi; // bi = row of the flip table for low bit b
+    double cz, cxy;
+};
+struct VTerm {    // Hubbard V n_i n_j
+    int i, j;
+    double v;
+};
+
+// Per-Hamiltonian descriptor (device copy read by every block at set-up).
+struct HamDesc {
+    int model;
+    int N, nlo, nhi;  // spin: bit split; Hubbard: N sites, nlo = N (down string bits)
+    int n;            // up spins (spin sector); -1 otherwise
+    int n_hh, n_lh, n_ncoef;
+    int n_v;
+    int ngroups;      // byte groups of the low half / down string
+    int64_t ddn;      // Hubbard: D_dn
+    HHBond hh[kMaxBond];
+    LHBond lh[kMaxLH];
+    VTerm v[kMaxBond];
+    double U[64];     // Hubbard on-site U per site
+    double coef[kMaxCoef];
+};
+
+// Lin tables of one species (spin string, or up / down fermion string).
+struct Species {
+    int N = 0, n = 0, nlo = 0, nhi = 0;
+    int64_t dim = 0;
+    uint32_t *ja = nullptr;      // [2^nlo] rank of l within its popcount class
+    uint64_t *jb = nullptr;      // [2^nhi] sector rows below h, ~0 if h occurs in no state
+    uint64_t *jbp = nullptr;     // [2^nhi + 1] the same count without the sentinel
+    uint32_t *loff = nullptr;    // [nlo + 2] first class position of each popcount
+    uint32_t *lstate = nullptr;  // [2^nlo] low halves ordered by (popcount, value)
+    uint32_t *states = nullptr;  // [dim] explicit states (Hubbard species), else null
+    std::vector<uint32_t> loff_h;
+};
+
+}  // namespace hphi
+
+struct hphi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    // reduction scratch: per-block partials and the reduced values
+    double *partials = nullptr;
+    size_t partials_n = 0;
+    double *dscal = nullptr;     // device scalars (reduced values, driver coefficients)
+    size_t dscal_n = 0;
+    double *hscal = nullptr;     // pinned host mirror of dscal
+    // driver vectors (Lanczos / TPQ), grown on demand
+    void *vec[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t vec_bytes = 0;
+    int *dflag = nullptr;        // device status word of consistency checks
+    // kernel timing: event pairs recorded around launches while profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+struct hphi_basis {
+    int model = 0, N = 0, nup = 0, ndn = 0;
+    int64_t D = 0;
+    int device = 0;
+    hphi::Species sp[2];
+};
+
+struct hphi_ham {
+    const hphi_basis *basis = nullptr;
+    int model = 0;
+    int device = 0;
+    int64_t D = 0;
+    int64_t nh = 0;              // number of blocks
+    int64_t L = 0;               // length of the per-class-position tables
+    int nlo = 0;
+    hphi::HamDesc host;          // host copy of the descriptor
+    hphi::HamDesc *desc = nullptr;
+    // per-class-position tables
+    double *dlow_d = nullptr;
+    float *dlow_f = nullptr;
+    uint8_t *ll_cnt = nullptr;
+    uint32_t *ll_tgt = nullptr;
+    uint16_t *ll_cf = nullptr;
+    int ll_w = 0;
+    uint32_t *flipq = nullptr;   // [nlb][L]
+    int nlb = 0;
+    // Hubbard up-string tables (per h)
+    uint8_t *up_cnt = nullptr;
+    uint32_t *up_tgt = nullptr;
+    uint16_t *up_cf = nullptr;
+    int up_w = 0;
+    double *aup = nullptr;       // diagonal part of the up string alone
+    int max_row_entries = 0;
+};
+
+namespace hphi {
+
+// ---- error helpers (capi.cu) ----------------------------------------------
+int set_err(hphi_ctx *ctx, int code, const char *fmt, ...);
+int cuda_err(hphi_ctx *ctx, cudaError_t e, const char *what);
+#define HPHI_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::hphi::cuda_err(ctx, _e, #call); \
+    } while (0)
+
+// ---- workspace (capi.cu) -------------------------------------------------------
+int ensure_partials(hphi_ctx *ctx, size_t n);
+int ensure_dscal(hphi_ctx *ctx, size_t n);
+int ensure_vecs(hphi_ctx *ctx, size_t bytes);
+
+// ---- kernel timing (capi.cu): returns a slot, -1 when not profiling ----------
+int prof_begin(hphi_ctx *ctx, int kind);
+void prof_end(hphi_ctx *ctx, int slot);
+enum ProfKind { PROF_HV = 0, PROF_VEC = 1 };
+
+// ---- basis (basis.cu) -----------------------------------------------------------
+int build_species(hphi_ctx *ctx, Species &sp, int N, int n, bool want_states);
+void free_species(Species &sp);
+
+// ---- H*x launch description (hv.cu) ------------------------------------------------
+struct HvLaunch {
+    int dtype_real;          // HPHI_F64 or HPHI_F32 (complex data passed as 2x real columns)
+    int ncol;                // real columns
+    const void *x;
+    int64_t ldx;             // in real elements
+    void *y;
+    int64_t ldy;
+    const void *v;           // optional third vector (gamma term), may alias y
+    int64_t ldv;
+    double beta;
+    const double *alpha_h;   // [ncol] host (nullptr: alpha_s for every column)
+    const double *gamma_h;   // [ncol] host (nullptr: gamma_s)
+    double alpha_s, gamma_s;
+    const double *coef_dev;  // device [2*ncol]: alpha_c then gamma_c; overrides host values
+    int red[3];              // reductions (Red codes)
+    double *partials;        // per 32-column slice: [grid][3][nc], slices back to back
+    int nslice;              // filled by the launcher
+    int sgrid[kMaxCols / 32];
+};
+int launch_hv(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L);
+// Upper bound of partials entries of one launch with ncol columns.
+size_t hv_partials_size(hphi_ctx *ctx, const hphi_ham *ham, int ncol);
+// Sums the partials of a finished launch: out_dev[r * ncol + c], r < 3.
+int reduce_hv(hphi_ctx *ctx, const HvLaunch &L, double *out_dev);
+
+// ---- reductions / vector kernels (vec.cu) ----------------------------------------------
+// Sums partials[grid][nval] over grid in fixed order into out_dev[nval].
+int reduce_partials(hphi_ctx *ctx, const double *partials, int grid, int nval, double *out_dev);
+int launch_dot(hphi_ctx *ctx, int real_dtype, int cplx, int64_t n, int nr, const void *x, int64_t ldx,
+               const void *y, int64_t ldy, double *out_dev /* nr (+ nr cross) */);
+// out = a[c] x[c] + b[c] x[c^1] + g[c] y[c]   (real columns; coefficient arrays host or device)
+struct LinComb {
+    int real_dtype;
+    int64_t n;
+    int nr;
+    const void *x;
+    int64_t ldx;
+    const void *y;
+    int64_t ldy;
+    void *out;
+    int64_t ldo;
+    const double *a_h, *b_h, *g_h;      // host [nr] (nullable -> 0)
+    const double *coef_dev;             // device [3*nr] (a, b, g) overrides
+    int red_oo;                          // also reduce sum out^2 per column
+    double *partials;
+    int grid;
+};
+int launch_lincomb(hphi_ctx *ctx, LinComb &L);
+int launch_random(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, uint64_t seed, void *x, int64_t ldx);
+int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x, int64_t ldx, void *y,
+                int64_t ldy);
+
+// ---- pattern (pattern.cu) --------------------------------------------------------
+int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,
+              std::vector<double> &vals, std::vector<int32_t> &cnt, int &stride);
+
+inline int real_of(int dtype) { return (dtype == HPHI_F64 || dtype == HPHI_C128) ? HPHI_F64 : HPHI_F32; }
+inline int is_complex(int dtype) { return dtype == HPHI_C128 || dtype == HPHI_C64; }
+inline size_t real_size(int real_dtype) { return real_dtype == HPHI_F64 ? 8 : 4; }
+inline bool valid_dtype(int d) { return d >= HPHI_F64 && d <= HPHI_C64; }
+
+}  // namespace hphi

@@ -1,0 +1,320 @@
+// Vector kernels around H*x: dot / nrm2 / axpy / scal (the Krylov and TPQ
+// bookkeeping of Sec. 1 and Sec. 3.5.1), start vectors, copies, and the
+// fixed-order reduction of per-block partial sums.
+//
+// Layout: n rows of nr real values, row stride ld (elements).  A row is
+// handled by TPR lanes (the smallest power of two >= nr, at most 32); lane t
+// takes the real columns t, t + TPR, ...  Grids are fixed for a given (n, nr),
+// so every reduction is summed in the same order on every call.
+#include <math.h>
+
+#include "hphi_internal.cuh"
+
+namespace hphi {
+
+namespace {
+
+struct FFv {
+    float hi, lo;
+};
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+    FFv s{0.f, 0.f};
+    __device__ __forceinline__ void add(float a, float b) {
+        float p = a * b, pe = fmaf(a, b, -p);
+        float t = s.hi + p, bp = t - s.hi;
+        float e = (s.hi - (t - bp)) + (p - bp);
+        s.hi = t;
+        s.lo += e + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
+};
+
+constexpr int kVT = 256;  // threads per block of the vector kernels
+
+inline int tpr_of(int nr) {
+    int t = 1;
+    while (t < nr && t < 32) t <<= 1;
+    return t;
+}
+
+// S[c] = sum_r x[r][c] y[r][c];  X[c] = sum_r x[r][c] y[r][c^1]  (if cross).
+// Lane `lane` of a row group owns columns lane + j*tpr, j < CPL; every
+// thread runs the same number of row iterations; the block sum is taken in
+// shared memory in a fixed order (group 0, 1, ...).
+template <typename T, int CPL>
+__global__ void __launch_bounds__(kVT) k_dot(int64_t n, int nr, int tpr, int cross, const T *__restrict__ x,
+                                             int64_t ldx, const T *__restrict__ y, int64_t ldy, double *partials) {
+    __shared__ double sm[2][kVT][CPL];
+    const int lane = threadIdx.x % tpr, grp = threadIdx.x / tpr, ngrp = kVT / tpr;
+    Acc<T> s[CPL], xs[CPL];
+    for (int64_t r0 = blockIdx.x * (int64_t)ngrp; r0 < n; r0 += (int64_t)gridDim.x * ngrp) {
+        const int64_t r = r0 + grp;
+        if (r >= n) continue;
+#pragma unroll
+        for (int j = 0; j < CPL; j++) {
+            const int c = lane + j * tpr;
+            if (c < nr) {
+                const T xv = x[r * ldx + c];
+                s[j].add(xv, y[r * ldy + c]);
+                if (cross) xs[j].add(xv, y[r * ldy + (c ^ 1)]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CPL; j++) {
+        sm[0][threadIdx.x][j] = s[j].value();
+        sm[1][threadIdx.x][j] = xs[j].value();
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * nr; t += blockDim.x) {
+        const int which = t / nr, c = t % nr, l = c % tpr, j = c / tpr;
+        double acc = 0.0;
+        for (int g = 0; g < ngrp; g++) acc += sm[which][g * tpr + l][j];
+        partials[((int64_t)blockIdx.x * 2 + which) * nr + c] = acc;
+    }
+}
+
+__global__ void k_reduce(const double *partials, int grid, int nval, double *out) {
+    for (int v = threadIdx.x; v < nval; v += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < grid; b++) s += partials[(int64_t)b * nval + v];
+        out[v] = s;
+    }
+}
+
+struct LCArgs {
+    int64_t n;
+    int nr, tpr, red;
+    const void *x;
+    int64_t ldx;
+    const void *y;
+    int64_t ldy;
+    void *out;
+    int64_t ldo;
+    const double *coef_dev;  // device [3][nr] (a, b, g); overrides the arrays below
+    double *partials;
+    double a[256], b[256], g[256];
+};
+
+template <typename T, int CPL>
+__global__ void __launch_bounds__(kVT) k_lincomb(const LCArgs A) {
+    __shared__ double sm[kVT][CPL];
+    __shared__ double cf[3][256];
+    for (int t = threadIdx.x; t < A.nr; t += blockDim.x) {
+        if (A.coef_dev) {
+            cf[0][t] = A.coef_dev[t];
+            cf[1][t] = A.coef_dev[A.nr + t];
+            cf[2][t] = A.coef_dev[2 * A.nr + t];
+        } else {
+            cf[0][t] = A.a[t];
+            cf[1][t] = A.b[t];
+            cf[2][t] = A.g[t];
+        }
+    }
+    __syncthreads();
+    const T *x = (const T *)A.x;
+    const T *y = (const T *)A.y;
+    T *o = (T *)A.out;
+    const int lane = threadIdx.x % A.tpr, grp = threadIdx.x / A.tpr, ngrp = kVT / A.tpr;
+    Acc<T> s[CPL];
+    // every thread runs the same number of iterations (uniform __syncwarp)
+    for (int64_t r0 = blockIdx.x * (int64_t)ngrp; r0 < A.n; r0 += (int64_t)gridDim.x * ngrp) {
+        const int64_t r = r0 + grp;
+        const bool rv = r < A.n;
+        T res[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; j++) {
+            const int c = lane + j * A.tpr;
+            if (rv && c < A.nr) {
+                T v = (T)cf[0][c] * x[r * A.ldx + c];
+                if (cf[1][c] != 0.0) v = fma((T)cf[1][c], x[r * A.ldx + (c ^ 1)], v);
+                if (y && cf[2][c] != 0.0) v = fma((T)cf[2][c], y[r * A.ldy + c], v);
+                res[j] = v;
+            }
+        }
+        __syncwarp();  // all lanes have read x[c^1] before any writes (in-place complex scal)
+#pragma unroll
+        for (int j = 0; j < CPL; j++) {
+            const int c = lane + j * A.tpr;
+            if (rv && c < A.nr) {
+                o[r * A.ldo + c] = res[j];
+                if (A.red) s[j].add(res[j], res[j]);
+            }
+        }
+        __syncwarp();
+    }
+    if (!A.red) return;
+#pragma unroll
+    for (int j = 0; j < CPL; j++) sm[threadIdx.x][j] = s[j].value();
+    __syncthreads();
+    for (int c = threadIdx.x; c < A.nr; c += blockDim.x) {
+        const int l = c % A.tpr, j = c / A.tpr;
+        double acc = 0.0;
+        for (int g = 0; g < ngrp; g++) acc += sm[g * A.tpr + l][j];
+        A.partials[(int64_t)blockIdx.x * A.nr + c] = acc;
+    }
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; r++) {
+        uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+template <typename T>
+__global__ void k_random(int64_t n, int nr, uint64_t seed, T *x, int64_t ldx) {
+    const int64_t total = n * nr;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)e, (uint32_t)((uint64_t)e >> 32), 0u, 0u};
+        philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        uint64_t wa = ((uint64_t)c[1] << 32) | c[0], wb = ((uint64_t)c[3] << 32) | c[2];
+        double ua = ((double)(wa >> 11) + 0.5) * 0x1.0p-53;
+        double ub = ((double)(wb >> 11) + 0.5) * 0x1.0p-53;
+        double z = sqrt(-2.0 * log(ua)) * cos(6.283185307179586 * ub);
+        int64_t r = e / nr;
+        int c0 = (int)(e - r * nr);
+        x[r * ldx + c0] = (T)z;
+    }
+}
+
+template <typename T>
+__global__ void k_copy(int64_t n, int nr, const T *x, int64_t ldx, T *y, int64_t ldy) {
+    const int64_t total = n * nr;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / nr;
+        int c = (int)(e - r * nr);
+        y[r * ldy + c] = x[r * ldx + c];
+    }
+}
+
+int vec_grid(hphi_ctx *ctx, int64_t n, int tpr) {
+    int64_t rows_per_block = kVT / tpr;
+    int64_t g = (n + rows_per_block - 1) / rows_per_block;
+    int64_t cap = (int64_t)ctx->sm_count * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+int reduce_partials(hphi_ctx *ctx, const double *partials, int grid, int nval, double *out_dev) {
+    k_reduce<<<1, 256, 0, ctx->stream>>>(partials, grid, nval, out_dev);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+int launch_dot(hphi_ctx *ctx, int real_dtype, int cplx, int64_t n, int nr, const void *x, int64_t ldx, const void *y,
+               int64_t ldy, double *out_dev) {
+    int tpr = tpr_of(nr);
+    int grid = vec_grid(ctx, n, tpr);
+    int st = ensure_partials(ctx, (size_t)grid * 2 * nr);
+    if (st) return st;
+    int slot = prof_begin(ctx, PROF_VEC);
+    const int cpl = (nr + tpr - 1) / tpr;
+#define HPHI_DOT(T, C)                                                                                         \
+    k_dot<T, C><<<grid, kVT, 0, ctx->stream>>>(n, nr, tpr, cplx, (const T *)x, ldx, (const T *)y, ldy, \
+                                               ctx->partials)
+    if (real_dtype == HPHI_F64) {
+        if (cpl <= 1) HPHI_DOT(double, 1);
+        else if (cpl <= 2) HPHI_DOT(double, 2);
+        else if (cpl <= 4) HPHI_DOT(double, 4);
+        else HPHI_DOT(double, 8);
+    } else {
+        if (cpl <= 1) HPHI_DOT(float, 1);
+        else if (cpl <= 2) HPHI_DOT(float, 2);
+        else if (cpl <= 4) HPHI_DOT(float, 4);
+        else HPHI_DOT(float, 8);
+    }
+#undef HPHI_DOT
+    prof_end(ctx, slot);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return reduce_partials(ctx, ctx->partials, grid, 2 * nr, out_dev);
+}
+
+int launch_lincomb(hphi_ctx *ctx, LinComb &L) {
+    LCArgs A;
+    A.n = L.n;
+    A.nr = L.nr;
+    A.tpr = tpr_of(L.nr);
+    A.red = L.red_oo;
+    A.x = L.x;
+    A.ldx = L.ldx;
+    A.y = L.y;
+    A.ldy = L.ldy;
+    A.out = L.out;
+    A.ldo = L.ldo;
+    A.coef_dev = L.coef_dev;
+    A.partials = L.partials;
+    L.grid = vec_grid(ctx, L.n, A.tpr);
+    for (int c = 0; c < 256; c++) {
+        A.a[c] = (c < L.nr && L.a_h) ? L.a_h[c] : 0.0;
+        A.b[c] = (c < L.nr && L.b_h) ? L.b_h[c] : 0.0;
+        A.g[c] = (c < L.nr && L.g_h) ? L.g_h[c] : 0.0;
+    }
+    int slot = prof_begin(ctx, PROF_VEC);
+    const int cpl = (L.nr + A.tpr - 1) / A.tpr;
+#define HPHI_LC(T, C) k_lincomb<T, C><<<L.grid, kVT, 0, ctx->stream>>>(A)
+    if (L.real_dtype == HPHI_F64) {
+        if (cpl <= 1) HPHI_LC(double, 1);
+        else if (cpl <= 2) HPHI_LC(double, 2);
+        else if (cpl <= 4) HPHI_LC(double, 4);
+        else HPHI_LC(double, 8);
+    } else {
+        if (cpl <= 1) HPHI_LC(float, 1);
+        else if (cpl <= 2) HPHI_LC(float, 2);
+        else if (cpl <= 4) HPHI_LC(float, 4);
+        else HPHI_LC(float, 8);
+    }
+#undef HPHI_LC
+    prof_end(ctx, slot);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+int launch_random(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, uint64_t seed, void *x, int64_t ldx) {
+    int64_t total = n * nr;
+    int64_t g = (total + 255) / 256;
+    if (g > (int64_t)ctx->sm_count * 16) g = (int64_t)ctx->sm_count * 16;
+    if (g < 1) g = 1;
+    if (real_dtype == HPHI_F64)
+        k_random<double><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nr, seed, (double *)x, ldx);
+    else
+        k_random<float><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nr, seed, (float *)x, ldx);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x, int64_t ldx, void *y, int64_t ldy) {
+    int64_t total = n * nr;
+    int64_t g = (total + 255) / 256;
+    if (g > (int64_t)ctx->sm_count * 16) g = (int64_t)ctx->sm_count * 16;
+    if (g < 1) g = 1;
+    if (real_dtype == HPHI_F64)
+        k_copy<double><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nr, (const double *)x, ldx, (double *)y, ldy);
+    else
+        k_copy<float><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nr, (const float *)x, ldx, (float *)y, ldy);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+}  // namespace hphi

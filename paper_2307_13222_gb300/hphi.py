@@ -1,0 +1,376 @@
+"""Thin ctypes binding of libhphi (include/hphi.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all
+computation happens in the CUDA library.  Device vectors are torch CUDA
+tensors, [D] or [D][nvec] with unit column stride; the library works on the
+caller's current torch stream.  There is no CPU path: without the built
+library or without a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhphi.so")
+
+HPHI_OK = 0
+ERRORS = {-1: "INVAL", -2: "NOMEM", -3: "CUDA", -4: "NOTCONV", -5: "NUMERIC", -6: "DEVICE_CHECK", -7: "TIMEOUT"}
+MODELS = {"SPIN_HALF": 0, "SPIN_HALF_GC": 1, "HUBBARD": 2}
+KINDS = {"EXCHANGE": 0, "XXZ": 1, "HOP": 2, "HUBBARD_U": 3, "DENS_DENS": 4}
+F64, F32, C128, C64 = 0, 1, 2, 3
+
+
+class HphiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hphi error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Term(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("i", C.c_int32), ("j", C.c_int32), ("spin", C.c_int32),
+                ("v0", C.c_double), ("v1", C.c_double)]
+
+
+class _LanczosOpts(C.Structure):
+    _fields_ = [("max_steps", C.c_int), ("tol", C.c_double), ("dtype", C.c_int), ("check_every", C.c_int)]
+
+
+class _LanczosResult(C.Structure):
+    _fields_ = [("e0", C.c_double), ("resid_est", C.c_double), ("resid", C.c_double), ("steps", C.c_int),
+                ("breakdown", C.c_int)]
+
+
+_lib = None
+vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+_SIGS = {
+    "hphi_ctx_create": (i32, [i32, vp, C.POINTER(vp)]),
+    "hphi_ctx_set_stream": (i32, [vp, vp]),
+    "hphi_ctx_destroy": (None, [vp]),
+    "hphi_last_error": (C.c_char_p, [vp]),
+    "hphi_ctx_sm_count": (i32, [vp]),
+    "hphi_ctx_profile": (i32, [vp, i32]),
+    "hphi_ctx_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl)]),
+    "hphi_build_basis": (i32, [vp, i32, i32, i32, i32, C.POINTER(vp)]),
+    "hphi_basis_destroy": (None, [vp]),
+    "hphi_basis_dim": (i64, [vp]),
+    "hphi_basis_table_sizes": (i32, [vp, i32, C.POINTER(i64), C.POINTER(i64)]),
+    "hphi_basis_export": (i32, [vp, vp, i32, vp, vp]),
+    "hphi_basis_states": (i32, [vp, vp, i64, i64, vp, vp]),
+    "hphi_basis_rank": (i32, [vp, vp, vp, vp, i64, vp]),
+    "hphi_build_hamiltonian": (i32, [vp, vp, vp, i32, C.POINTER(vp)]),
+    "hphi_ham_destroy": (None, [vp]),
+    "hphi_ham_dim": (i64, [vp]),
+    "hphi_apply_H": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, dbl, dbl]),
+    "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
+    "hphi_dot": (i32, [vp, i32, i64, i32, vp, i64, vp, i64, vp]),
+    "hphi_nrm2": (i32, [vp, i32, i64, i32, vp, i64, vp]),
+    "hphi_axpy": (i32, [vp, i32, i64, i32, vp, vp, i64, vp, i64]),
+    "hphi_scal": (i32, [vp, i32, i64, i32, vp, vp, i64]),
+    "hphi_random_vector": (i32, [vp, i32, i64, i32, C.c_uint64, vp, i64]),
+    "hphi_lanczos": (i32, [vp, vp, C.POINTER(_LanczosOpts), vp, vp, vp, vp, C.POINTER(_LanczosResult)]),
+    "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libhphi.so (built by paper_2307_13222_gb300.build); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libhphi not built ({path} missing): run paper_2307_13222_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _np(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.float64: F64, torch.float32: F32, torch.complex128: C128, torch.complex64: C64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _vec(t):
+    """(pointer, nvec, ld) of a [D] or [D][nvec] CUDA tensor with unit column stride."""
+    if not t.is_cuda:
+        raise ValueError("libhphi takes CUDA tensors only (no CPU path)")
+    if t.dim() == 1:
+        if t.stride(0) != 1:
+            raise ValueError("vector must be contiguous")
+        return C.c_void_p(t.data_ptr()), 1, 1
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected [D] or [D][nvec] with unit column stride")
+    return C.c_void_p(t.data_ptr()), t.shape[1], max(t.stride(0), t.shape[1])
+
+
+class Context:
+    """A library context on one CUDA device, following torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: libhphi has no CPU fallback")
+        self.lib = load_library()
+        self.device = device
+        h = vp()
+        torch.cuda.set_device(device)
+        torch.cuda.init()
+        st = self.lib.hphi_ctx_create(device, C.c_void_p(torch.cuda.current_stream(device).cuda_stream), C.byref(h))
+        if st != HPHI_OK:
+            raise HphiError(st, "hphi_ctx_create failed")
+        self.h = h
+
+    def _sync_stream(self):
+        import torch
+        self.lib.hphi_ctx_set_stream(self.h, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def check(self, st: int):
+        if st != HPHI_OK:
+            raise HphiError(st, (self.lib.hphi_last_error(self.h) or b"").decode())
+
+    @property
+    def sm_count(self) -> int:
+        return int(self.lib.hphi_ctx_sm_count(self.h))
+
+    def profile(self, enable: bool = True):
+        """Record CUDA-event times around every kernel launch of this context."""
+        self.check(self.lib.hphi_ctx_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, kind: int = 0):
+        """(launches, total_ms) of kernel class kind (0: H*x, 1: vector kernels) since the last read."""
+        n, t = i64(0), dbl(0.0)
+        self.check(self.lib.hphi_ctx_profile_read(self.h, kind, C.byref(n), C.byref(t)))
+        return int(n.value), float(t.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hphi_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Basis:
+    def __init__(self, ctx: Context, model: str, n_sites: int, n_up: int = 0, n_dn: int = 0):
+        self.ctx = ctx
+        ctx._sync_stream()
+        h = vp()
+        ctx.check(ctx.lib.hphi_build_basis(ctx.h, MODELS[model], n_sites, n_up, n_dn, C.byref(h)))
+        self.h = h
+        self.model, self.n_sites, self.n_up, self.n_dn = model, n_sites, n_up, n_dn
+        self.dim = int(ctx.lib.hphi_basis_dim(h))
+
+    def export_tables(self, species: int = 0):
+        na, nb = i64(0), i64(0)
+        self.ctx.check(self.ctx.lib.hphi_basis_table_sizes(self.h, species, C.byref(na), C.byref(nb)))
+        ja = np.zeros(na.value, np.uint32)
+        jb = np.zeros(nb.value, np.uint64)
+        self.ctx._sync_stream()
+        self.ctx.check(self.ctx.lib.hphi_basis_export(self.ctx.h, self.h, species, _np(ja), _np(jb)))
+        return ja, jb
+
+    def states(self, row0: int, n: int):
+        import torch
+        su = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.ctx.device}")
+        sd = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.ctx.device}")
+        self.ctx._sync_stream()
+        self.ctx.check(self.ctx.lib.hphi_basis_states(self.ctx.h, self.h, row0, n, C.c_void_p(su.data_ptr()),
+                                                      C.c_void_p(sd.data_ptr())))
+        return su, sd
+
+    def rank(self, su, sd=None):
+        import torch
+        n = su.numel()
+        out = torch.empty(n, dtype=torch.int64, device=su.device)
+        self.ctx._sync_stream()
+        self.ctx.check(self.ctx.lib.hphi_basis_rank(self.ctx.h, self.h, C.c_void_p(su.data_ptr()),
+                                                    C.c_void_p(sd.data_ptr()) if sd is not None else None, n,
+                                                    C.c_void_p(out.data_ptr())))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hphi_basis_destroy(self.h)
+            self.h = None
+
+
+class Hamiltonian:
+    def __init__(self, ctx: Context, basis: Basis, terms):
+        self.ctx, self.basis = ctx, basis
+        arr = (_Term * max(len(terms), 1))()
+        for k, (kind, i, j, spin, v0, v1) in enumerate(terms):
+            arr[k] = _Term(KINDS[kind], i, j, spin, v0, v1)
+        ctx._sync_stream()
+        h = vp()
+        ctx.check(ctx.lib.hphi_build_hamiltonian(ctx.h, basis.h, C.cast(arr, vp), len(terms), C.byref(h)))
+        self.h = h
+        self.dim = int(ctx.lib.hphi_ham_dim(h))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hphi_ham_destroy(self.h)
+            self.h = None
+
+
+# ---- entry points with the C names -------------------------------------------------
+
+def hphi_apply_H(ham: Hamiltonian, x, y, alpha: float = 1.0, beta: float = 0.0):
+    """y <- alpha H x + beta y (asynchronous on the current stream)."""
+    ctx = ham.ctx
+    if x.dtype != y.dtype or x.shape != y.shape:
+        raise ValueError("x and y must have the same dtype and shape")
+    px, nv, ldx = _vec(x)
+    py, _, ldy = _vec(y)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_apply_H(ctx.h, ham.h, _dtype_code(x), nv, px, ldx, py, ldy, float(alpha), float(beta)))
+    return y
+
+
+def hphi_dot(ctx: Context, x, y) -> np.ndarray:
+    px, nv, ldx = _vec(x)
+    py, _, ldy = _vec(y)
+    dc = _dtype_code(x)
+    out = np.zeros(2 * nv if dc in (C128, C64) else nv)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_dot(ctx.h, dc, x.shape[0], nv, px, ldx, py, ldy, _np(out)))
+    if dc in (C128, C64):
+        return out[0::2] + 1j * out[1::2]
+    return out
+
+
+def hphi_nrm2(ctx: Context, x) -> np.ndarray:
+    px, nv, ldx = _vec(x)
+    out = np.zeros(nv)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_nrm2(ctx.h, _dtype_code(x), x.shape[0], nv, px, ldx, _np(out)))
+    return out
+
+
+def _coefs(a, nv, cplx):
+    a = np.atleast_1d(np.asarray(a, dtype=np.complex128 if cplx else np.float64))
+    if a.size == 1:
+        a = np.repeat(a, nv)
+    return np.ascontiguousarray(a.view(np.float64) if cplx else a)
+
+
+def hphi_axpy(ctx: Context, a, x, y):
+    px, nv, ldx = _vec(x)
+    py, _, ldy = _vec(y)
+    dc = _dtype_code(x)
+    av = _coefs(a, nv, dc in (C128, C64))
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_axpy(ctx.h, dc, x.shape[0], nv, _np(av), px, ldx, py, ldy))
+    return y
+
+
+def hphi_scal(ctx: Context, a, x):
+    px, nv, ldx = _vec(x)
+    dc = _dtype_code(x)
+    av = _coefs(a, nv, dc in (C128, C64))
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_scal(ctx.h, dc, x.shape[0], nv, _np(av), px, ldx))
+    return x
+
+
+def hphi_random_vector(ctx: Context, x, seed: int):
+    px, nv, ldx = _vec(x)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_random_vector(ctx.h, _dtype_code(x), x.shape[0], nv, C.c_uint64(seed), px, ldx))
+    return x
+
+
+def hphi_lanczos(ham: Hamiltonian, v0, max_steps: int, tol: float, check_every: int = 1, gs_out=None):
+    """Lanczos from v0 (F64 or F32 CUDA vector). Returns a dict; NOTCONV is reported, not raised."""
+    ctx = ham.ctx
+    dc = _dtype_code(v0)
+    opts = _LanczosOpts(max_steps, tol, dc, check_every)
+    res = _LanczosResult()
+    alpha = np.zeros(max_steps)
+    beta = np.zeros(max_steps + 1)
+    ctx._sync_stream()
+    st = ctx.lib.hphi_lanczos(ctx.h, ham.h, C.byref(opts), C.c_void_p(v0.data_ptr()),
+                              C.c_void_p(gs_out.data_ptr()) if gs_out is not None else None, _np(alpha), _np(beta),
+                              C.byref(res))
+    if st not in (HPHI_OK, -4):
+        ctx.check(st)
+    m = res.steps
+    return dict(converged=st == HPHI_OK, status=st, e0=res.e0, resid_est=res.resid_est, resid=res.resid, steps=m,
+                breakdown=bool(res.breakdown), alpha=alpha[:m], beta=beta[1:m + 1])
+
+
+def hphi_tpq_step(ham: Hamiltonian, V, dtau: float, nmax: int, norm2: np.ndarray):
+    """One cTPQ step in place on V; norm2 (float64[nvec]) is updated in place.
+    Returns (e, h2, logd) per column."""
+    ctx = ham.ctx
+    pv, nv, ld = _vec(V)
+    assert norm2.dtype == np.float64 and norm2.size == nv and norm2.flags.c_contiguous
+    e, h2, logd = np.zeros(nv), np.zeros(nv), np.zeros(nv)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_tpq_step(ctx.h, ham.h, _dtype_code(V), nv, pv, ld, float(dtau), int(nmax), _np(norm2),
+                                    _np(e), _np(h2), _np(logd)))
+    return e, h2, logd
+
+
+def hphi_dump_pattern(ham: Hamiltonian, row0: int, row1: int):
+    """Merged, column-sorted pattern of rows [row0, row1) as host CSR arrays."""
+    ctx = ham.ctx
+    n = row1 - row0
+    rowptr = np.zeros(n + 1, np.int64)
+    cap = i64(0)
+    ctx._sync_stream()
+    st = ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, _np(rowptr), None, None, C.byref(cap))
+    if st not in (HPHI_OK, -1) or cap.value <= 0:
+        ctx.check(st)
+    cols = np.zeros(cap.value, np.int64)
+    vals = np.zeros(cap.value, np.float64)
+    ctx.check(ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, _np(rowptr), _np(cols), _np(vals), C.byref(cap)))
+    return rowptr, cols[:cap.value], vals[:cap.value]
+
+
+def hphi_tridiag_eigen(a, b):
+    """Eigenvalues (ascending) and eigenvectors (columns) of the tridiagonal
+    with diagonal a and off-diagonal b[1:]; host-only, no GPU needed."""
+    lib = load_library()
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    n = a.size
+    ev = np.zeros(n)
+    Z = np.zeros((n, n))
+    st = lib.hphi_tridiag_eigen(n, _np(a), _np(b), _np(ev), _np(Z))
+    if st != HPHI_OK:
+        raise HphiError(st, "tridiagonal eigensolver failed")
+    return ev, Z
+
+
+def write_matrix_market(f, n: int, rowptr, cols, vals, row0: int = 0, comment: str = "hphi"):
+    """Write rows of a pattern in the Matrix Market layout the paper prints
+    (Sec. 3.1.2): a '%' comment line, 'rows cols nnz', then 1-based
+    'l m re im' lines."""
+    nnz = int(rowptr[-1] - rowptr[0])
+    f.write(f"% {comment}\n{n} {n} {nnz} \n")
+    for r in range(len(rowptr) - 1):
+        for k in range(rowptr[r], rowptr[r + 1]):
+            v = complex(vals[k])
+            re, im = v.real + 0.0, v.imag + 0.0  # no negative zeros
+            f.write(f"{row0 + r + 1} {int(cols[k]) + 1} {re!r}  {im!r}\n")

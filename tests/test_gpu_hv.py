@@ -1,0 +1,178 @@
+"""GPU H*x against the oracle, element by element.
+
+Tolerances: FP64 results agree with the oracle's FP64 sums to a few ulps of
+the row magnitude (different summation order): 1e-13 relative to max|y|.
+FP32 storage/arithmetic: the inputs are rounded to FP32 (2^-24) and each row
+sums <= ~70 terms, so 2e-6 relative to max|y|."""
+import itertools
+import random
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import pair, rel_err
+from paper_2307_13222_gb300 import hphi
+from workloads import (chain, square, heisenberg_terms, hubbard_terms, random_regular_graph, uniform_couplings,
+                       random_vectors)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-13, torch.float32: 2e-6, torch.complex128: 1e-13, torch.complex64: 2e-6}
+
+
+def _check(m, h, dtype, nvec, alpha=1.0, beta=0.0, ld_pad=0, seed=0):
+    cplx = dtype in (torch.complex128, torch.complex64)
+    x = random_vectors(m.dim, nvec, seed + 11, complex_=cplx, normalize=False)
+    y0 = random_vectors(m.dim, nvec, seed + 12, complex_=cplx, normalize=False)
+    ld = nvec + ld_pad
+    xd = torch.zeros((m.dim, ld), dtype=dtype, device="cuda")
+    yd = torch.zeros((m.dim, ld), dtype=dtype, device="cuda")
+    xd[:, :nvec] = torch.from_numpy(x).to(dtype)
+    yd[:, :nvec] = torch.from_numpy(y0).to(dtype)
+    xs, ys = xd[:, :nvec], yd[:, :nvec]
+    hphi.hphi_apply_H(h, xs, ys, alpha, beta)
+    # oracle on the same (rounded) inputs
+    xr = xs.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    yr0 = torch.from_numpy(y0).to(dtype).numpy().astype(np.complex128 if cplx else np.float64)
+    if cplx:
+        want = np.empty_like(xr)
+        want.real = m.apply(np.ascontiguousarray(xr.real), alpha, beta, np.ascontiguousarray(yr0.real))
+        want.imag = m.apply(np.ascontiguousarray(xr.imag), alpha, beta, np.ascontiguousarray(yr0.imag))
+    else:
+        want = m.apply(xr, alpha, beta, yr0.copy())
+    got = ys.cpu().numpy()
+    assert rel_err(got, want) < TOL[dtype], (dtype, nvec, rel_err(got, want))
+    if ld_pad:  # padding columns untouched
+        assert (yd[:, nvec:] == 0).all()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nvec", [1, 2, 3, 8, 32, 33])
+def test_spin_chain_sector(dtype, nvec):
+    m, b, h = pair("SPIN_HALF", 14, 7, 0, heisenberg_terms(chain(14), 1.0))
+    _check(m, h, dtype, nvec, alpha=0.7, beta=-0.3 if nvec % 2 else 0.0, seed=nvec)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.complex128, torch.complex64])
+def test_random_xxz_sector(dtype):
+    rng = random.Random(5)
+    N = 15
+    pairs = rng.sample(list(itertools.combinations(range(N), 2)), 40)
+    terms = [("XXZ", i, j, 0, rng.uniform(-1, 2), rng.uniform(-1, 2)) for i, j in pairs]
+    m, b, h = pair("SPIN_HALF", N, 6, 0, terms)
+    _check(m, h, dtype, 2, alpha=1.3, beta=0.5, ld_pad=3, seed=2)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nvec", [1, 4, 16])
+def test_full_space_random_graph(dtype, nvec):
+    bonds = random_regular_graph(14, 3, 9)
+    terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 10))
+    m, b, h = pair("SPIN_HALF_GC", 14, 0, 0, terms)
+    _check(m, h, dtype, nvec, seed=3)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.complex128])
+@pytest.mark.parametrize("geom", ["chain8", "square3x3", "random"])
+def test_hubbard(dtype, geom):
+    if geom == "chain8":
+        N, terms = 8, hubbard_terms(8, chain(8), t=1.0, U=4.0)
+        nu, nd = 4, 3
+    elif geom == "square3x3":
+        N, terms = 9, hubbard_terms(9, square(3, 3), t=0.8, U=6.0, V=0.5)
+        nu, nd = 4, 5
+    else:
+        rng = random.Random(7)
+        N = 8
+        terms = [("HOP", j, i, rng.choice([-1, 0, 1]), rng.uniform(-1, 1), 0.0)
+                 for i, j in rng.sample(list(itertools.combinations(range(N), 2)), 12)]
+        terms += [("HUBBARD_U", i, i, 0, rng.uniform(0, 5), 0.0) for i in range(N)]
+        terms += [("DENS_DENS", 1, 6, 0, -0.4, 0.0)]
+        nu, nd = 3, 4
+    m, b, h = pair("HUBBARD", N, nu, nd, terms)
+    _check(m, h, dtype, 1, alpha=-0.9, beta=0.25, seed=4)
+
+
+def test_edge_cases():
+    # one-state sectors, no terms, two sites
+    for (model, N, nu, terms) in [("SPIN_HALF", 6, 6, heisenberg_terms(chain(6), 1.0)),
+                                  ("SPIN_HALF", 6, 0, heisenberg_terms(chain(6), 1.0)),
+                                  ("SPIN_HALF", 6, 3, []), ("SPIN_HALF", 2, 1, heisenberg_terms([(0, 1)], 1.0)),
+                                  ("SPIN_HALF_GC", 2, 0, heisenberg_terms([(0, 1)], 2.0))]:
+        m, b, h = pair(model, N, nu, 0, terms)
+        _check(m, h, torch.float64, 1)
+    m, b, h = pair("HUBBARD", 4, 0, 0, hubbard_terms(4, chain(4), 1.0, 3.0))
+    _check(m, h, torch.float64, 1)
+    m, b, h = pair("HUBBARD", 4, 4, 4, hubbard_terms(4, chain(4), 1.0, 3.0))
+    _check(m, h, torch.float64, 1)
+
+
+def test_alias_and_bad_arguments_rejected():
+    m, b, h = pair("SPIN_HALF", 10, 5, 0, heisenberg_terms(chain(10), 1.0))
+    x = torch.ones(m.dim, dtype=torch.float64, device="cuda")
+    with pytest.raises(hphi.HphiError):
+        hphi.hphi_apply_H(h, x, x)
+    y = torch.ones(m.dim + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        hphi.hphi_apply_H(h, x, y)
+
+
+def test_hermitian_on_gpu():
+    m, b, h = pair("SPIN_HALF", 20, 10, 0, heisenberg_terms(square(5, 4), 1.0))
+    u = torch.from_numpy(random_vectors(m.dim, 1, 1)[:, 0]).cuda()
+    v = torch.from_numpy(random_vectors(m.dim, 1, 2)[:, 0]).cuda()
+    hu, hv = torch.empty_like(u), torch.empty_like(v)
+    hphi.hphi_apply_H(h, u, hu)
+    hphi.hphi_apply_H(h, v, hv)
+    a, c = torch.dot(u, hv).item(), torch.dot(hu, v).item()
+    assert abs(a - c) < 1e-13 * max(abs(a), 1.0)
+
+
+def _sampled_rows(m, h, dtype, nvec, rows, seed):
+    """Full-size check: x drawn on the device, y at sampled rows from the
+    oracle's row entries and the gathered x values."""
+    ctx = h.ctx
+    x = torch.empty((m.dim, nvec) if nvec > 1 else (m.dim,), dtype=dtype, device="cuda")
+    hphi.hphi_random_vector(ctx, x, seed)
+    y = torch.empty_like(x)
+    hphi.hphi_apply_H(h, x, y)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for r in rows:
+        cols, vals, _ = m.row_entries(int(r))
+        xv = x[torch.from_numpy(cols).cuda()].cpu().numpy().astype(np.float64)
+        want = (vals[:, None] * xv.reshape(len(cols), -1)).sum(axis=0)
+        got = y[int(r)].cpu().numpy().astype(np.float64).reshape(-1)
+        scale = np.abs(vals).sum() * np.abs(xv).max()
+        worst = max(worst, float(np.abs(got - want).max() / scale))
+    del x, y
+    torch.cuda.empty_cache()
+    return worst
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_square_4x8_full_size_sampled(dtype):
+    """The N=32 S^z=0 sector of the 4x8 lattice (601,080,390 rows)."""
+    m, b, h = pair("SPIN_HALF", 32, 16, 0, heisenberg_terms(square(8, 4), 1.0))
+    rng = np.random.default_rng(8)
+    rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
+    assert _sampled_rows(m, h, dtype, 1, rows, 42) < (1e-15 if dtype == torch.float64 else 1e-6)
+
+
+def test_hubbard_4x4_full_size_sampled():
+    m, b, h = pair("HUBBARD", 16, 8, 8, hubbard_terms(16, square(4, 4), t=1.0, U=8.0))
+    rng = np.random.default_rng(9)
+    rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 300)])
+    assert _sampled_rows(m, h, torch.float64, 1, rows, 43) < 1e-15
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rrg26_block32_full_size_sampled(dtype):
+    """2^26 rows x 32 real columns (16 complex TPQ vectors)."""
+    bonds = random_regular_graph(26, 3, 4)
+    terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 1004))
+    m, b, h = pair("SPIN_HALF_GC", 26, 0, 0, terms)
+    rng = np.random.default_rng(10)
+    rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 200)])
+    assert _sampled_rows(m, h, dtype, 32, rows, 44) < (1e-15 if dtype == torch.float64 else 1e-6)

@@ -1,0 +1,76 @@
+"""GPU Lanczos against the oracle's Lanczos and dense diagonalisation."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import pair
+from paper_2307_13222_gb300 import hphi
+from workloads import chain, square, heisenberg_terms, hubbard_terms, random_vectors, configs, uniform_couplings
+
+pytestmark = pytest.mark.gpu
+
+
+def test_chain16_sz0_fp64():
+    """N=16 periodic Heisenberg chain, S^z=0 (12,870 states), FP64, residual 1e-12."""
+    cfg = configs.heisenberg_chain16()
+    m, b, h = pair(cfg["model"], cfg["n_sites"], cfg["n_up"], 0, cfg["terms"])
+    v0 = random_vectors(m.dim, 1, cfg["seed"])[:, 0]
+    ro = m.lanczos(v0, cfg["max_steps"], cfg["tol"], want_gs=True)
+    gs = torch.empty(m.dim, dtype=torch.float64, device="cuda")
+    r = hphi.hphi_lanczos(h, torch.from_numpy(v0).cuda(), cfg["max_steps"], cfg["tol"], gs_out=gs)
+    assert r["converged"] and ro["status"] == 0
+    assert abs(r["e0"] - ro["e0"]) <= 1e-10 * abs(ro["e0"])
+    assert abs(np.dot(gs.cpu().numpy(), ro["gs"])) >= 1 - 1e-10
+    assert r["resid"] < 1e-9
+    # alpha/beta agree with the oracle's recurrence along the run
+    k = min(r["steps"], ro["steps"], 40)
+    assert np.allclose(r["alpha"][:k], ro["alpha"][:k], rtol=1e-9, atol=1e-9)
+
+
+def test_chain16_fp32_storage_error_stated():
+    cfg = configs.heisenberg_chain16()
+    m, b, h = pair(cfg["model"], cfg["n_sites"], cfg["n_up"], 0, cfg["terms"])
+    v0 = random_vectors(m.dim, 1, cfg["seed"])[:, 0]
+    ro = m.lanczos(v0, 300, 1e-12)
+    gs = torch.empty(m.dim, dtype=torch.float32, device="cuda")
+    r = hphi.hphi_lanczos(h, torch.from_numpy(v0).float().cuda(), 300, 1e-6, gs_out=gs)
+    err = abs(r["e0"] - ro["e0"]) / abs(ro["e0"])
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("N,seed", [(10, 1), (12, 2)])
+def test_random_chain_vs_dense(N, seed):
+    terms = heisenberg_terms(chain(N), uniform_couplings(N, 0.5, 1.5, seed))
+    m, b, h = pair("SPIN_HALF", N, N // 2, 0, terms)
+    w = np.linalg.eigvalsh(O.dense_matrix(m))
+    r = hphi.hphi_lanczos(h, torch.from_numpy(random_vectors(m.dim, 1, 3)[:, 0]).cuda(), 300, 1e-12)
+    assert r["converged"] and abs(r["e0"] - w[0]) < 1e-10 * abs(w[0])
+
+
+def test_hubbard_chain_vs_oracle():
+    terms = hubbard_terms(8, chain(8), t=1.0, U=4.0)
+    m, b, h = pair("HUBBARD", 8, 4, 4, terms)
+    v0 = random_vectors(m.dim, 1, 5)[:, 0]
+    ro = m.lanczos(v0, 300, 1e-12)
+    r = hphi.hphi_lanczos(h, torch.from_numpy(v0).cuda(), 300, 1e-12)
+    assert r["converged"] and abs(r["e0"] - ro["e0"]) < 1e-10 * abs(ro["e0"])
+
+
+def test_two_state_breakdown_and_notconv():
+    m, b, h = pair("SPIN_HALF", 2, 1, 0, heisenberg_terms([(0, 1)]))
+    r = hphi.hphi_lanczos(h, torch.tensor([1.0, 0.3], device="cuda", dtype=torch.float64), 10, 1e-12)
+    assert r["breakdown"] and r["steps"] == 2 and abs(r["e0"] + 0.75) < 1e-14
+    m, b, h = pair("SPIN_HALF", 14, 7, 0, heisenberg_terms(chain(14)))
+    r = hphi.hphi_lanczos(h, torch.from_numpy(random_vectors(m.dim, 1, 1)[:, 0]).cuda(), 5, 1e-14)
+    assert not r["converged"] and r["status"] == -4 and r["steps"] == 5
+    with pytest.raises(hphi.HphiError):
+        hphi.hphi_lanczos(h, torch.zeros(m.dim, dtype=torch.float64, device="cuda"), 5, 1e-12)
+
+
+def test_deterministic_bitwise():
+    m, b, h = pair("SPIN_HALF", 18, 9, 0, heisenberg_terms(chain(18)))
+    v0 = torch.from_numpy(random_vectors(m.dim, 1, 1)[:, 0]).cuda()
+    r1 = hphi.hphi_lanczos(h, v0, 40, 0.0, check_every=40)
+    r2 = hphi.hphi_lanczos(h, v0, 40, 0.0, check_every=7)
+    assert np.array_equal(r1["alpha"], r2["alpha"]) and np.array_equal(r1["beta"], r2["beta"])
