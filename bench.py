@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: Lanczos steps on the 4x8 Heisenberg S^z=0 sector.
+
+Workload: spin-1/2 Heisenberg J1 model on the 4x8 periodic square lattice
+(N=32, site = x + 8y), S^z=0 sector, D = C(32,16) = 601,080,390 rows.  One
+step is one Lanczos iteration through hphi_lanczos: the fused H*x kernel
+(u = H w_k / beta_k - beta_k/beta_{k-1} w_{k-1} with <w_k, u>), the vector
+pass (w_{k+1} = u - alpha_k/beta_k w_k with |w_{k+1}|^2), and the device-side
+alpha/beta bookkeeping.  The timed region is one hphi_lanczos call of K steps
+(its start-vector copy and norm, and the final host tridiagonal solve,
+included).
+
+metric: H*x GB/s = steps * (algorithmic H*x bytes: read x + write y, 8 B/row
+per FP32 vector / 16 B/row FP64) / time, summed over ranks.  Vectors are FP32
+by default (FP64 alpha/beta and reductions); --dtype f64 runs FP64 vectors,
+and the default run also measures the FP64 path and reports it under "fp64".
+
+--impl reference times the CPU oracle (plain C, OpenMP row loop) on a bounded
+row sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+D_4X8 = 601080390
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds: float = 15.0):
+    """The CPU oracle's H*x over a bounded contiguous row sample of the 4x8
+    S^z=0 workload; returns (GB/s H*x-equivalent, threads, sample text)."""
+    import numpy as np
+    import oracle as O
+    from workloads import configs
+    O.build()
+    cfg = configs.heisenberg_square4x8()
+    m = O.Model("SPIN_HALF", 32, 16, 0, cfg["terms"])
+    x = np.zeros(m.dim)  # lazily mapped; the values do not change the oracle's work
+    y = np.zeros(m.dim)
+    r0 = m.dim // 3
+    n = 20000
+    t0 = time.perf_counter()
+    m.apply(x, y=y, rows=(r0, r0 + n))
+    dt = time.perf_counter() - t0
+    n = int(min(m.dim - r0, max(n, n * seconds / max(dt, 1e-6))))
+    return m, x, y, r0, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    m, x, y, r0, n = oracle_sample(seconds=max(2.0, 20.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        m.apply(x, y=y, rows=(r0, r0 + n))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m.apply(x, y=y, rows=(r0, r0 + n))
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = 16.0 * n / dt / 1e9
+    sample = f"oracle H*x (pull form, FP64) over rows [{r0}, {r0 + n}) of the 4x8 S^z=0 sector per step"
+    line = {"impl": "reference", "metric": "hv_gbps", "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "heisenberg_square_4x8_Sz0", "n_sites": 32, "dim": D_4X8,
+                       "sample_rows": n, "l2": "host run"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def lanczos_steps(ham, v0, steps):
+    from paper_2307_13222_gb300 import hphi
+    return hphi.hphi_lanczos(ham, v0, steps, 0.0, check_every=steps)
+
+
+def measure_dtype(ctx, ham, dim, dtype_name, K, W, dist, world):
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    tdt = torch.float32 if dtype_name == "f32" else torch.float64
+    es = 4 if dtype_name == "f32" else 8
+    v0 = torch.empty(dim, dtype=tdt, device="cuda")
+    hphi.hphi_random_vector(ctx, v0, 2)
+    lanczos_steps(ham, v0, max(W, 1))
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    ctx.profile_read(1)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    r = lanczos_steps(ham, v0, K)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    hv_n, hv_ms = ctx.profile_read(0)
+    vec_n, vec_ms = ctx.profile_read(1)
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    del v0
+    torch.cuda.empty_cache()
+    total_bytes = world * K * 2.0 * es * dim
+    return dict(ms=ms, wall_s=wall, value=total_bytes / (ms * 1e-3) / 1e9, hv_launches=hv_n, hv_ms=hv_ms,
+                vec_launches=vec_n, vec_ms=vec_ms, e0=r["e0"], steps=r["steps"], es=es)
+
+
+def measure_e2e(ctx, ham, dim, dtype_name, K):
+    """H*x through the public API with host buffers: per step H2D of x from
+    pinned memory, hphi_apply_H, D2H of y into pinned memory."""
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    tdt = torch.float32 if dtype_name == "f32" else torch.float64
+    es = 4 if dtype_name == "f32" else 8
+    xh = torch.empty(dim, dtype=tdt, pin_memory=True)
+    yh = torch.empty(dim, dtype=tdt, pin_memory=True)
+    xd = torch.empty(dim, dtype=tdt, device="cuda")
+    hphi.hphi_random_vector(ctx, xd, 3)
+    xh.copy_(xd)
+    yd = torch.empty_like(xd)
+    torch.cuda.synchronize()
+    steps = max(1, min(K, 3))
+    for _ in range(1):
+        xd.copy_(xh, non_blocking=True)
+        hphi.hphi_apply_H(ham, xd, yd)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        xd.copy_(xh, non_blocking=True)
+        hphi.hphi_apply_H(ham, xd, yd)
+        yh.copy_(yd, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del xh, yh, xd, yd
+    torch.cuda.empty_cache()
+    return dict(value=2.0 * es * dim / (ms * 1e-3) / 1e9, ms=ms, h2d=es * dim, d2h=es * dim)
+
+
+def run_native(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    import paper_2307_13222_gb300 as P
+    from paper_2307_13222_gb300 import hphi
+    from workloads import configs
+    if rank == 0 or not os.path.exists(P.LIBRARY_PATH):
+        P.build()
+    if dist:
+        dist.barrier()
+    ctx = hphi.Context(local)
+    cfg = configs.heisenberg_square4x8()
+    basis = hphi.Basis(ctx, "SPIN_HALF", 32, 16)
+    ham = hphi.Hamiltonian(ctx, basis, cfg["terms"])
+    dim = basis.dim
+    K, W = args.steps, args.warmup
+    clocks = ClockSampler(local)
+    clocks.start()
+    main = measure_dtype(ctx, ham, dim, args.dtype, K, W, dist, world)
+    ck = clocks.stop()
+    other = None
+    if args.dtype == "f32" and not args.no_fp64:
+        other = measure_dtype(ctx, ham, dim, "f64", max(2, K // 4), 1, dist, world)
+    e2e = measure_e2e(ctx, ham, dim, args.dtype, K) if not args.no_e2e else None
+    peak, peak_kind = peaks()
+    # dominant kernel: the fused H*x of the Lanczos step; algorithmic bytes per
+    # launch = gather x + read w_{k-1} + write u = 3 vectors (24 B/row FP64, 12 B/row FP32)
+    hv_avg_ms = main["hv_ms"] / max(main["hv_launches"], 1)
+    kern_bytes = 3.0 * main["es"] * dim
+    achieved = kern_bytes / (hv_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"hv_traffic_{args.dtype}.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                traffic = json.load(f).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        m, x, y, r0, n = oracle_sample(seconds=15.0)
+        t0 = time.perf_counter()
+        m.apply(x, y=y, rows=(r0, r0 + n))
+        dt = time.perf_counter() - t0
+        cpu = {"value": 16.0 * n / dt / 1e9, "unit": "GB/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"oracle H*x (pull form, FP64) over rows [{r0}, {r0 + n}) of the same sector, "
+                         f"{dt:.1f} s"}
+    gpu_launches = 7 * K + 4
+    line = {
+        "metric": "hv_gbps", "value": main["value"], "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": main["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": "heisenberg_square_4x8_Sz0", "n_sites": 32, "dim": dim, "step": "lanczos_iteration",
+                   "vectors": args.dtype, "scalars": "f64", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (one vector = %.1f GB)" % (main["es"] * dim / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_hv (fused Lanczos H*x)",
+                     "peak_kind": peak_kind, "avg_launch_ms": hv_avg_ms},
+        "gpu_launches": gpu_launches,
+        "kernel_ms": {"hv": main["hv_ms"], "vector": main["vec_ms"], "hv_launches": main["hv_launches"],
+                      "vector_launches": main["vec_launches"]},
+        "lanczos_e0_after_steps": main["e0"],
+    }
+    if ck:
+        line["clocks"] = ck
+    if e2e:
+        line["e2e"] = {"value": e2e["value"], "unit": "GB/s", "h2d_bytes_per_step": e2e["h2d"],
+                       "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"], "step": "hphi_apply_H"}
+    if other:
+        a64 = 3.0 * 8 * dim / ((other["hv_ms"] / max(other["hv_launches"], 1)) * 1e-3) / 1e9
+        line["fp64"] = {"value": other["value"], "ms_per_step": other["ms"] / max(2, K // 4),
+                        "hv_kernel_gbps": a64, "frac": a64 / peak}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.profile(False)
+    del ham, basis
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the extra FP64 measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("steps >= 1, warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -30,6 +30,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
@@ -59,6 +62,16 @@ static int orc_popcount(uint64_t x)
 
 static int64_t binom_table[65][65];
 static int binom_ready = 0;
+
+/* Threads the OpenMP row loop of orc_apply uses (1 without OpenMP). */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Pascal's triangle, C(n, k) for 0 <= k <= n <= 64 (C(64, 32) < 2^63). */
 int64_t orc_binom(int n, int k)

@@ -52,6 +52,7 @@ def _L():
         lib = C.CDLL(build())
         i64, i32, dbl, vp = C.c_int64, C.c_int, C.c_double, C.c_void_p
         sig = {
+            "orc_num_threads": (i32, []),
             "orc_binom": (i64, [i32, i32]),
             "orc_dim": (i64, [i32, i32, i32, i32]),
             "orc_enumerate": (i64, [i32, i32, vp, i64]),
@@ -85,6 +86,11 @@ def _L():
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    """Threads of the oracle's OpenMP row loop."""
+    return int(_L().orc_num_threads())
 
 
 def binom(n: int, k: int) -> int:
