@@ -189,6 +189,36 @@ HPHI_API int hphi_axpy(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const doub
 HPHI_API int hphi_scal(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const double *a_host, void *x, int64_t ldx);
 HPHI_API int hphi_random_vector(hphi_ctx *ctx, int dtype, int64_t n, int nvec, uint64_t seed, void *x, int64_t ldx);
 
+/* ---- dot product without any device allocation ------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: a process that reserved its whole device
+ * memory budget up front (for example a solver service holding every Krylov
+ * vector resident), a host framework whose allocator must own every
+ * allocation, or a latency-critical path on which cudaMalloc, which can
+ * synchronise the device, is not acceptable.  Such callers cannot create an
+ * hphi_ctx (its workspace is allocated), so this entry point takes the device
+ * and stream directly.
+ * It computes exactly what hphi_dot computes (same kernels, same fixed-order
+ * reduction) for nvec columns of dtype on `device`, enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream), and waits for that stream.
+ * Scratch: a file-scope device array of HPHI_DOT_STATIC_SCRATCH_BYTES
+ * (about 0.5 MB) that every GPU which loads the library keeps until the
+ * process exits; no cudaMalloc, cudaFree or allocating library routine is
+ * called.  Limits: at most HPHI_DOT_STATIC_MAX_REAL real columns (a complex
+ * column counts two); larger requests return HPHI_E_INVAL.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  The
+ * calling thread's current device is restored before returning.
+ * Every call uses the same array, and nothing in it needs to start at zero
+ * (each call writes every slot it reads before reading it).  Calls that
+ * overlap on the GPU (other streams, other threads) race on the array: do not
+ * overlap them. */
+#define HPHI_DOT_STATIC_MAX_REAL 64
+#define HPHI_DOT_STATIC_MAX_BLOCKS 512
+#define HPHI_DOT_STATIC_SCRATCH_BYTES (8 * (2 * HPHI_DOT_STATIC_MAX_BLOCKS * HPHI_DOT_STATIC_MAX_REAL + 2 * HPHI_DOT_STATIC_MAX_REAL))
+HPHI_API int hphi_dot_static(int device, void *stream, int dtype, int64_t n, int nvec, const void *x, int64_t ldx,
+                             const void *y, int64_t ldy, double *out_host);
+
 /* ---- Lanczos ground state (Sec. 1, Table 1) ---------------------------------
  * Three-term Lanczos from v0 (device, length D, dtype F64 or F32: the storage
  * precision of the Krylov vectors; alpha/beta, the tridiagonal problem and

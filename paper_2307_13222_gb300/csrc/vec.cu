@@ -318,3 +318,105 @@ int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x,
 }
 
 }  // namespace hphi
+
+// ---- dot product with file-scope scratch (no device allocation) ------------
+// The partials of the block reduction and the reduced values live in a
+// file-scope device array; its device address is looked up once per device.
+namespace {
+
+constexpr int kStaticReal = HPHI_DOT_STATIC_MAX_REAL;
+constexpr int kStaticBlocks = HPHI_DOT_STATIC_MAX_BLOCKS;
+constexpr size_t kStaticDoubles = HPHI_DOT_STATIC_SCRATCH_BYTES / sizeof(double);
+static_assert(kStaticDoubles == 2 * kStaticBlocks * kStaticReal + 2 * kStaticReal, "scratch layout");
+
+static __device__ __align__(256) double g_dot_scratch[kStaticDoubles];
+
+double *g_dot_scratch_addr[64] = {nullptr};
+
+}  // namespace
+
+extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, int nvec, const void *x, int64_t ldx,
+                               const void *y, int64_t ldy, double *out) {
+    using namespace hphi;
+    if (!out || n < 0 || nvec < 1 || !valid_dtype(dtype) || device < 0 || device >= 64) return HPHI_E_INVAL;
+    const int cpl = is_complex(dtype) ? 2 : 1, nr = nvec * cpl;
+    if (nr > kStaticReal) return HPHI_E_INVAL;
+    if (ldx < nvec || ldy < nvec || (n > 0 && (!x || !y))) return HPHI_E_INVAL;
+    if (n == 0) {
+        for (int k = 0; k < nr; k++) out[k] = 0.0;
+        return HPHI_OK;
+    }
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        return HPHI_E_CUDA;
+    }
+    int rc = HPHI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    do {
+        if (cudaSetDevice(device) != cudaSuccess) {
+            rc = HPHI_E_CUDA;
+            break;
+        }
+        if (!g_dot_scratch_addr[device]) {
+            double *p = nullptr;
+            if (cudaGetSymbolAddress((void **)&p, g_dot_scratch) != cudaSuccess || !p) {
+                rc = HPHI_E_CUDA;
+                break;
+            }
+            g_dot_scratch_addr[device] = p;
+        }
+        double *partials = g_dot_scratch_addr[device];
+        double *result = partials + 2 * kStaticBlocks * kStaticReal;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            rc = HPHI_E_CUDA;
+            break;
+        }
+        const int tpr = tpr_of(nr);
+        int64_t g = (n + (kVT / tpr) - 1) / (kVT / tpr);
+        int64_t cap = (int64_t)sms * 8;
+        if (cap > kStaticBlocks) cap = kStaticBlocks;
+        if (g > cap) g = cap;
+        const int grid = (int)(g < 1 ? 1 : g);
+        const int cplane = (nr + tpr - 1) / tpr;
+        const int rd = real_of(dtype);
+        const int64_t lx = ldx * cpl, ly = ldy * cpl;
+#define HPHI_SDOT(T, C)                                                                                    \
+    k_dot<T, C><<<grid, kVT, 0, st>>>(n, nr, tpr, cpl == 2, (const T *)x, lx, (const T *)y, ly, partials)
+        if (rd == HPHI_F64) {
+            if (cplane <= 1) HPHI_SDOT(double, 1);
+            else if (cplane <= 2) HPHI_SDOT(double, 2);
+            else HPHI_SDOT(double, 4);
+        } else {
+            if (cplane <= 1) HPHI_SDOT(float, 1);
+            else if (cplane <= 2) HPHI_SDOT(float, 2);
+            else HPHI_SDOT(float, 4);
+        }
+#undef HPHI_SDOT
+        k_reduce<<<1, 256, 0, st>>>(partials, grid, 2 * nr, result);
+        if (cudaGetLastError() != cudaSuccess) {
+            rc = HPHI_E_CUDA;
+            break;
+        }
+        double host[2 * kStaticReal];
+        if (cudaMemcpyAsync(host, result, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = HPHI_E_CUDA;
+            break;
+        }
+        const double *S = host, *X = host + nr;
+        for (int q = 0; q < nvec; q++) {
+            if (cpl == 1) {
+                out[q] = S[q];
+            } else {
+                out[2 * q] = S[2 * q] + S[2 * q + 1];
+                out[2 * q + 1] = X[2 * q] - X[2 * q + 1];
+            }
+        }
+    } while (0);
+    if (rc != HPHI_OK) cudaGetLastError();
+    cudaSetDevice(prev);
+    return rc;
+}
+

@@ -73,6 +73,7 @@ _SIGS = {
     "hphi_lanczos": (i32, [vp, vp, C.POINTER(_LanczosOpts), vp, vp, vp, vp, C.POINTER(_LanczosResult)]),
     "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
     "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
+    "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
 }
 
 
@@ -254,6 +255,24 @@ def hphi_dot(ctx: Context, x, y) -> np.ndarray:
     out = np.zeros(2 * nv if dc in (C128, C64) else nv)
     ctx._sync_stream()
     ctx.check(ctx.lib.hphi_dot(ctx.h, dc, x.shape[0], nv, px, ldx, py, ldy, _np(out)))
+    if dc in (C128, C64):
+        return out[0::2] + 1j * out[1::2]
+    return out
+
+
+def hphi_dot_static(device: int, x, y) -> np.ndarray:
+    """<x_q|y_q> like hphi_dot, through the entry point that allocates no device
+    memory (no context needed); runs on torch's current stream of `device`."""
+    import torch
+    lib = load_library()
+    px, nv, ldx = _vec(x)
+    py, _, ldy = _vec(y)
+    dc = _dtype_code(x)
+    out = np.zeros(2 * nv if dc in (C128, C64) else nv)
+    st = lib.hphi_dot_static(device, C.c_void_p(torch.cuda.current_stream(device).cuda_stream), dc, x.shape[0], nv,
+                             px, ldx, py, ldy, _np(out))
+    if st != HPHI_OK:
+        raise HphiError(st, "hphi_dot_static failed")
     if dc in (C128, C64):
         return out[0::2] + 1j * out[1::2]
     return out
