@@ -152,6 +152,27 @@ HPHI_API int hphi_build_hamiltonian(hphi_ctx *ctx, const hphi_basis *basis, cons
 HPHI_API void hphi_ham_destroy(hphi_ham *ham);
 HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
 
+/* ---- launch tuning of a Hamiltonian ------------------------------------------
+ * Knobs of the H*x kernel for this Hamiltonian (all launches that use it):
+ *   HPHI_TUNE_INNER_BITS  high-half bits of the row-block traversal varied
+ *                         first (an L2-resident subcube); -1 = automatic
+ *   HPHI_TUNE_SPLIT       thread blocks that share one row block (1..8),
+ *                         fewer row blocks in flight for the same occupancy
+ *   HPHI_TUNE_L2_HINTS    1 = L2 eviction-priority hints on gathers/streams
+ *   HPHI_TUNE_VARIANT     -1 = automatic (default); spin models: 1 = neighbour
+ *                         ranks computed on the fly from Lin's ja table, 0 =
+ *                         precomputed neighbour lists (also enables the
+ *                         one-thread-per-row kernel for Hubbard)
+ * Results do not depend on the knobs except through summation order of the
+ * reductions (still deterministic for fixed knobs).  HPHI_E_INVAL for an
+ * unknown knob or value. */
+#define HPHI_TUNE_INNER_BITS 0
+#define HPHI_TUNE_SPLIT 1
+#define HPHI_TUNE_L2_HINTS 2
+#define HPHI_TUNE_VARIANT 3
+HPHI_API int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value);
+HPHI_API int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value);
+
 /* ---- H*x (the hot path) -------------------------------------------------
  * y <- alpha * H x + beta * y for nvec columns (1 <= nvec <= 128 real
  * columns; a complex column counts as two).  x and y are device arrays of
@@ -235,6 +256,10 @@ typedef struct hphi_lanczos_opts {
     double tol;
     int dtype;       /* HPHI_F64 or HPHI_F32 */
     int check_every; /* host convergence check period in steps (>= 1) */
+    int reorth;      /* 0: three-term recurrence (two passes for the vector);
+                        1: full reorthogonalisation, classical Gram-Schmidt
+                        applied twice against every stored Krylov vector
+                        (the library allocates (max_steps + 1) vectors) */
 } hphi_lanczos_opts;
 
 typedef struct hphi_lanczos_result {

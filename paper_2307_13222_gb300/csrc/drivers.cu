@@ -113,9 +113,34 @@ __global__ void k_lz(int mode, int k, const double *red, double *alpha, double *
     }
 }
 
-struct LzBuffers {
-    double *alpha = nullptr, *beta2 = nullptr;
-};
+// scalar bookkeeping of the reorthogonalising recurrence (normalised vectors)
+enum RzMode { RZ_INIT = 0, RZ_PREP = 1, RZ_ALPHA = 2, RZ_BETA = 3 };
+
+__global__ void k_rz(int mode, int k, const double *red, double *alpha, double *beta2, double *coef, int *flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == RZ_INIT) {
+        beta2[0] = red[0];
+        if (!(red[0] > 0.0) || !isfinite(red[0])) *flag = -1;
+        coef[0] = 1.0 / sqrt(red[0]);  // scale of v_0
+        coef[1] = 0.0;
+        coef[2] = 0.0;
+    } else if (mode == RZ_PREP) {
+        coef[0] = 1.0;                               // alpha of H*x
+        coef[1] = k > 0 ? -sqrt(beta2[k]) : 0.0;     // gamma: -beta_k v_{k-1}
+    } else if (mode == RZ_ALPHA) {
+        alpha[k] = red[0];
+        coef[0] = -red[0];  // u -= alpha_k v_k
+        coef[1] = 0.0;
+        coef[2] = 1.0;
+        if (!isfinite(red[0]) && *flag == 0) *flag = k + 1;
+    } else {
+        beta2[k + 1] = red[0];
+        coef[0] = 1.0 / sqrt(red[0]);  // v_{k+1} = u / beta_{k+1}
+        coef[1] = 0.0;
+        coef[2] = 0.0;
+        if ((!(red[0] >= 0.0) || !isfinite(red[0])) && *flag == 0) *flag = k + 1;
+    }
+}
 
 }  // namespace
 
@@ -144,6 +169,183 @@ extern "C" int hphi_tridiag_eigen(int n, const double *a, const double *b, doubl
     return HPHI_OK;
 }
 
+// Lanczos with full reorthogonalisation: every normalised Krylov vector is kept
+// and each new direction is projected out of all of them twice (classical
+// Gram-Schmidt, twice is enough), with FP64 projection coefficients.
+static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0,
+                          void *gs_out, double *alpha_host, double *beta_host, hphi_lanczos_result *res) {
+    const int dt = opts->dtype, M = opts->max_steps;
+    const int check = opts->check_every < 1 ? 1 : opts->check_every;
+    const int64_t D = ham->D;
+    const size_t es = real_size(dt), vb = (size_t)D * es;
+    int st;
+    if ((st = ensure_vecs(ctx, vb))) return st;
+    size_t np = hv_partials_size(ctx, ham, 1);
+    if (np < (size_t)ctx->sm_count * 8 * 2) np = (size_t)ctx->sm_count * 8 * 2;
+    if ((st = ensure_partials(ctx, np))) return st;
+    char *Vb = nullptr;
+    double *sc = nullptr;
+    cudaError_t e = cudaMalloc((void **)&Vb, vb * ((size_t)M + 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, HPHI_E_NOMEM, "reorthogonalisation needs %zu bytes for %d Krylov vectors",
+                       vb * ((size_t)M + 1), M + 1);
+    }
+    e = cudaMalloc((void **)&sc, sizeof(double) * (4 * (size_t)M + 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(Vb);
+        return set_err(ctx, HPHI_E_NOMEM, "reorthogonalisation scalars");
+    }
+    double *alpha_d = sc, *beta2_d = sc + M + 1, *cbuf = sc + 2 * (size_t)M + 4;  // cbuf: M + 1 entries
+    double *coefA = ctx->dscal + 3000, *coefB = ctx->dscal + 3008, *red = ctx->dscal + 3016;
+    auto V = [&](int j) -> void * { return Vb + (size_t)j * vb; };
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(Vb);
+        cudaFree(sc);
+        return code;
+    };
+    void *u = ctx->vec[0];
+    std::vector<double> alpha_h(M + 1, 0.0), beta2_h(M + 2, 0.0), y;
+    int steps = 0, conv = 0, brk = 0;
+    double theta = 0.0, resid_est = -1.0;
+    auto lincomb = [&](const void *x, const void *yv, void *out, const double *cdev, int red_oo) -> int {
+        LinComb B{};
+        B.real_dtype = dt;
+        B.n = D;
+        B.nr = 1;
+        B.x = x;
+        B.ldx = 1;
+        B.y = yv;
+        B.ldy = 1;
+        B.out = out;
+        B.ldo = 1;
+        B.coef_dev = cdev;
+        B.red_oo = red_oo;
+        B.partials = ctx->partials;
+        int s2 = launch_lincomb(ctx, B);
+        if (!s2 && red_oo) s2 = reduce_partials(ctx, ctx->partials, B.grid, 1, red);
+        return s2;
+    };
+    HPHI_CUDA(ctx, cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+    if ((st = launch_copy(ctx, dt, D, 1, v0, 1, V(0), 1))) return fail(st);
+    if ((st = launch_dot(ctx, dt, 0, D, 1, V(0), 1, V(0), 1, red))) return fail(st);
+    k_rz<<<1, 32, 0, ctx->stream>>>(RZ_INIT, 0, red, alpha_d, beta2_d, coefB, ctx->dflag);
+    if ((st = lincomb(V(0), nullptr, V(0), coefB, 0))) return fail(st);
+    for (int k = 0; k < M; k++) {
+        k_rz<<<1, 32, 0, ctx->stream>>>(RZ_PREP, k, red, alpha_d, beta2_d, coefA, ctx->dflag);
+        HvLaunch A{};
+        A.dtype_real = dt;
+        A.ncol = 1;
+        A.x = V(k);
+        A.ldx = 1;
+        A.y = u;
+        A.ldy = 1;
+        A.v = k > 0 ? V(k - 1) : nullptr;
+        A.ldv = 1;
+        A.coef_dev = coefA;
+        A.red[0] = R_XO;
+        A.partials = ctx->partials;
+        if ((st = launch_hv(ctx, ham, A)) || (st = reduce_hv(ctx, A, red))) return fail(st);
+        k_rz<<<1, 32, 0, ctx->stream>>>(RZ_ALPHA, k, red, alpha_d, beta2_d, coefB, ctx->dflag);
+        if ((st = lincomb(V(k), u, u, coefB, 0))) return fail(st);
+        for (int pass = 0; pass < 2; pass++) {
+            if ((st = launch_mdot(ctx, dt, D, k + 1, Vb, u, cbuf)) ||
+                (st = launch_maxpy(ctx, dt, D, k + 1, Vb, cbuf, u)))
+                return fail(st);
+        }
+        if ((st = launch_dot(ctx, dt, 0, D, 1, u, 1, u, 1, red))) return fail(st);
+        k_rz<<<1, 32, 0, ctx->stream>>>(RZ_BETA, k, red, alpha_d, beta2_d, coefB, ctx->dflag);
+        if ((st = lincomb(u, nullptr, V(k + 1), coefB, 0))) return fail(st);
+        HPHI_CUDA(ctx, cudaGetLastError());
+        steps = k + 1;
+        if ((k + 1) % check == 0 || k + 1 == M) {
+            int flag = 0;
+            HPHI_CUDA(ctx, cudaMemcpyAsync(alpha_h.data(), alpha_d, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaMemcpyAsync(beta2_h.data(), beta2_d, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            HPHI_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            if (flag == -1) return fail(set_err(ctx, HPHI_E_INVAL, "Lanczos: start vector has zero norm"));
+            int mstop = k + 1;
+            double tn = 0.0;
+            for (int j = 0; j <= k; j++) {
+                double r = fabs(alpha_h[j]) + (j > 0 ? sqrt(beta2_h[j]) : 0.0) + sqrt(beta2_h[j + 1]);
+                tn = r > tn ? r : tn;
+                if (sqrt(beta2_h[j + 1]) <= 64.0 * DBL_EPSILON * tn) {
+                    mstop = j + 1;
+                    brk = 1;
+                    break;
+                }
+            }
+            if (flag > 0 && !(brk && mstop <= flag - 1))
+                return fail(set_err(ctx, HPHI_E_NUMERIC, "Lanczos: non-finite scalars at step %d", flag - 1));
+            std::vector<double> a(alpha_h.begin(), alpha_h.begin() + mstop), b(mstop, 0.0), ev(mstop),
+                Z((size_t)mstop * mstop);
+            for (int j = 1; j < mstop; j++) b[j] = sqrt(beta2_h[j]);
+            if ((st = hphi_tridiag_eigen(mstop, a.data(), b.data(), ev.data(), Z.data())))
+                return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
+            theta = ev[0];
+            y.assign(mstop, 0.0);
+            for (int i = 0; i < mstop; i++) y[i] = Z[(size_t)i * mstop];
+            resid_est = sqrt(beta2_h[mstop]) * fabs(y[mstop - 1]);
+            steps = mstop;
+            if (brk) break;
+            if (opts->tol > 0.0 && mstop >= 2 && resid_est <= opts->tol * (fabs(theta) > 1.0 ? fabs(theta) : 1.0)) {
+                conv = 1;
+                break;
+            }
+        }
+    }
+    const int m = steps;
+    res->e0 = theta;
+    res->resid_est = resid_est;
+    res->resid = -1.0;
+    res->steps = m;
+    res->breakdown = brk;
+    if (alpha_host)
+        for (int j = 0; j < M; j++) alpha_host[j] = j < m ? alpha_h[j] : 0.0;
+    if (beta_host)
+        for (int j = 0; j <= M; j++) beta_host[j] = (j >= 1 && j <= m) ? sqrt(beta2_h[j]) : 0.0;
+    if (gs_out) {
+        // x = sum_j y_j v_j, as gs -= sum_j (-y_j) v_j from zero
+        std::vector<double> ny(m);
+        for (int j = 0; j < m; j++) ny[j] = -y[j];
+        HPHI_CUDA(ctx, cudaMemcpyAsync(cbuf, ny.data(), sizeof(double) * m, cudaMemcpyHostToDevice, ctx->stream));
+        HPHI_CUDA(ctx, cudaMemsetAsync(gs_out, 0, vb, ctx->stream));
+        if ((st = launch_maxpy(ctx, dt, D, m, Vb, cbuf, gs_out))) return fail(st);
+        double nrm = 0.0;
+        if ((st = hphi_nrm2(ctx, dt, D, 1, gs_out, 1, &nrm))) return fail(st);
+        if (!(nrm > 0.0)) return fail(set_err(ctx, HPHI_E_NUMERIC, "ground-state vector has zero norm"));
+        double inv = 1.0 / nrm;
+        if ((st = hphi_scal(ctx, dt, D, 1, &inv, gs_out, 1))) return fail(st);
+        HvLaunch R{};
+        R.dtype_real = dt;
+        R.ncol = 1;
+        R.x = gs_out;
+        R.ldx = 1;
+        R.y = u;
+        R.ldy = 1;
+        R.v = gs_out;
+        R.ldv = 1;
+        R.alpha_s = 1.0;
+        R.gamma_s = -theta;
+        R.red[0] = R_OO;
+        R.partials = ctx->partials;
+        if ((st = launch_hv(ctx, ham, R)) || (st = reduce_hv(ctx, R, red))) return fail(st);
+        double rr = 0.0;
+        HPHI_CUDA(ctx, cudaMemcpyAsync(&rr, red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        res->resid = sqrt(rr);
+    }
+    fail(HPHI_OK);
+    if (opts->tol > 0.0 && !conv && !brk)
+        return set_err(ctx, HPHI_E_NOTCONV, "Lanczos: tolerance not reached in %d steps", m);
+    return HPHI_OK;
+}
+
 extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0,
                             void *gs_out, double *alpha_host, double *beta_host, hphi_lanczos_result *res) {
     if (!ctx || !ham || !opts || !v0 || !res) return HPHI_E_INVAL;
@@ -156,7 +358,9 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
     const int64_t D = ham->D;
     const size_t es = real_size(dt);
     if (ham->device != ctx->device) return set_err(ctx, HPHI_E_INVAL, "hamiltonian belongs to another device");
+    if (opts->reorth != 0 && opts->reorth != 1) return set_err(ctx, HPHI_E_INVAL, "reorth must be 0 or 1");
     HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (opts->reorth) return lanczos_reorth(ctx, ham, opts, v0, gs_out, alpha_host, beta_host, res);
     int st;
     if ((st = ensure_vecs(ctx, (size_t)D * es))) return st;
     size_t np = hv_partials_size(ctx, ham, 1);

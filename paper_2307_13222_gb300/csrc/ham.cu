@@ -32,6 +32,17 @@ struct LLBond {
     double cxy;
 };
 
+__global__ void k_ja16(const uint32_t *ja, int64_t n, uint16_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (uint16_t)ja[i];
+}
+
+// Packs ELL entries as target | coefficient index << 24 when both fit.
+__global__ void k_pack_ll(const uint32_t *tgt, const uint16_t *cf, int64_t n, uint32_t *pk) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pk[i] = (tgt[i] & 0xFFFFFFu) | ((uint32_t)cf[i] << 24);
+}
+
 __global__ void k_spin_tables(int sector, const uint32_t *lstate, const uint32_t *ja, int64_t L, double c0,
                               const LLBond *ll, int nll, const int *lowbits, int nlb, double *dlow_d, float *dlow_f,
                               uint8_t *cnt, uint32_t *tgt, uint16_t *cf, uint32_t *flipq) {
@@ -126,6 +137,8 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->up_tgt);
     cudaFree(h->up_cf);
     cudaFree(h->aup);
+    cudaFree(h->ll_pk);
+    cudaFree(h->ja16);
     delete h;
 }
 
@@ -193,6 +206,9 @@ int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) 
         }
     }
     if ((int)ll.size() > 255) return set_err(ctx, HPHI_E_INVAL, "too many low-low bonds (max 255)");
+    if ((int)ll.size() > kMaxBond) return set_err(ctx, HPHI_E_INVAL, "too many low-low bonds (max %d)", kMaxBond);
+    for (size_t k = 0; k < ll.size(); k++) D.ll[k] = LLBondD{ll[k].i, ll[k].j, ll[k].cz, ll[k].cxy};
+    D.n_ll = (int)ll.size();
     D.n_hh = nhh;
     D.n_lh = nlh;
     D.n_ncoef = ncoef;
@@ -255,6 +271,7 @@ int build_hubbard(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_term
     }
     HamDesc &D = H->host;
     D.model = HPHI_HUBBARD;
+    D.n_ll = 0;
     D.N = N;
     D.nlo = N;
     D.nhi = 0;
@@ -348,6 +365,28 @@ extern "C" int hphi_build_hamiltonian(hphi_ctx *ctx, const hphi_basis *basis, co
         if (!st) {
             cudaError_t e = cudaMemcpy(H->desc, &H->host, sizeof(HamDesc), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = cuda_err(ctx, e, "descriptor copy");
+        }
+    }
+    // 16-bit copy of Lin's ja for the on-the-fly ranks of the H*x kernel
+    if (!st && basis->model == HPHI_SPIN_HALF && basis->sp[0].nlo <= 16) {
+        const size_t n = (size_t)1 << basis->sp[0].nlo;
+        st = dev_alloc(ctx, &H->ja16, n);
+        if (!st) {
+            k_ja16<<<grid_of((int64_t)n), 256, 0, ctx->stream>>>(basis->sp[0].ja, (int64_t)n, H->ja16);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) st = cuda_err(ctx, e, "k_ja16");
+        }
+    }
+    // packed low-low lists: target < 2^24 and coefficient index < 256
+    if (!st && H->ll_w > 0 && H->L < (1 << 24) && H->host.n_ncoef <= 256) {
+        const size_t n = (size_t)H->L * H->ll_w;
+        st = dev_alloc(ctx, &H->ll_pk, n);
+        if (!st) {
+            k_pack_ll<<<grid_of((int64_t)n), 256, 0, ctx->stream>>>(H->ll_tgt, H->ll_cf, (int64_t)n, H->ll_pk);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) st = cuda_err(ctx, e, "k_pack_ll");
         }
     }
     if (st) {

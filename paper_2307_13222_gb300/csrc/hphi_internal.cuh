@@ -53,6 +53,10 @@ struct LHBond {   // spin bond between high bit a and low bit b
     int a, b, bi; // bi = row of the flip table for low bit b
     double cz, cxy;
 };
+struct LLBondD {  // spin bond with both sites in the low half
+    int i, j;
+    double cz, cxy;
+};
 struct VTerm {    // Hubbard V n_i n_j
     int i, j;
     double v;
@@ -69,6 +73,8 @@ struct HamDesc {
     int64_t ddn;      // Hubbard: D_dn
     HHBond hh[kMaxBond];
     LHBond lh[kMaxLH];
+    LLBondD ll[kMaxBond];
+    int n_ll;
     VTerm v[kMaxBond];
     double U[64];     // Hubbard on-site U per site
     double coef[kMaxCoef];
@@ -142,7 +148,14 @@ struct hphi_ham {
     uint16_t *up_cf = nullptr;
     int up_w = 0;
     double *aup = nullptr;       // diagonal part of the up string alone
+    uint32_t *ll_pk = nullptr;   // packed low-low lists (target | coefficient index << 24)
+    uint16_t *ja16 = nullptr;    // Lin's ja as 16-bit ranks (spin sector, N_lo <= 16)
     int max_row_entries = 0;
+    // launch tuning (hphi_ham_set_tuning)
+    int tune_inner = -1;
+    int tune_split = 1;
+    int tune_hints = 1;
+    int tune_variant = -1;       // -1: automatic, 1: on-the-fly ranks (spin), 0: table-driven
 };
 
 namespace hphi {
@@ -186,9 +199,11 @@ struct HvLaunch {
     double alpha_s, gamma_s;
     const double *coef_dev;  // device [2*ncol]: alpha_c then gamma_c; overrides host values
     int red[3];              // reductions (Red codes)
-    double *partials;        // per 32-column slice: [grid][3][nc], slices back to back
-    int nslice;              // filled by the launcher
-    int sgrid[kMaxCols / 32];
+    double *partials;        // per column slice: [grid][3][nc], slices back to back
+    int nslice;              // column slices launched (filled by the launcher)
+    int sgrid[kMaxCols];     // grid of slice s
+    int sc0[kMaxCols];       // first column of slice s
+    int snc[kMaxCols];       // columns of slice s
 };
 int launch_hv(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L);
 // Upper bound of partials entries of one launch with ncol columns.
@@ -220,6 +235,10 @@ struct LinComb {
 };
 int launch_lincomb(hphi_ctx *ctx, LinComb &L);
 int launch_random(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, uint64_t seed, void *x, int64_t ldx);
+// c[j] = <V_j, w> for nv vectors stored back to back (V_j at V + j*n), into out_dev[nv]
+int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const void *w, double *out_dev);
+// w -= sum_j c_dev[j] V_j
+int launch_maxpy(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const double *c_dev, void *w);
 int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x, int64_t ldx, void *y,
                 int64_t ldy);
 

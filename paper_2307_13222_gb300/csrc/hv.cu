@@ -10,39 +10,11 @@
 // gathered.  Thread blocks walk the row blocks h in a fixed interleaved order.
 #include <type_traits>
 
-#include "rowvisit.cuh"
+#include "hvcommon.cuh"
 
 namespace hphi {
 
 namespace {
-
-struct FF {  // float-float accumulator (Knuth TwoSum + exact FMA product)
-    float hi, lo;
-};
-__device__ __forceinline__ void ff_add_prod(FF &s, float a, float b) {
-    float p = a * b;
-    float pe = fmaf(a, b, -p);
-    float t = s.hi + p;
-    float bp = t - s.hi;
-    float e = (s.hi - (t - bp)) + (p - bp);
-    s.hi = t;
-    s.lo += e + pe;
-}
-
-template <typename T>
-struct RedAcc;
-template <>
-struct RedAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct RedAcc<float> {
-    FF s{0.f, 0.f};
-    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(s, a, b); }
-    __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
-};
 
 template <typename T, int CPL>
 __device__ __forceinline__ void load_cols(const T *p, T (&v)[CPL]) {
@@ -143,25 +115,6 @@ struct HvSink {
     }
 };
 
-template <typename T>
-struct HvArgs {
-    HvTables P;
-    const T *x;
-    int64_t ldx;
-    T *y;
-    int64_t ldy;
-    const T *v;
-    int64_t ldv;
-    int ncol;  // columns of this launch (<= 32)
-    double beta;
-    double alpha[32];
-    double gamma[32];
-    const double *alpha_dev;  // override alpha[] when non-null
-    const double *gamma_dev;
-    int red[3];
-    double *partials;  // [grid][3][ncol]
-};
-
 template <typename T, int G, int CPL>
 __global__ void __launch_bounds__(kThreads) k_hv(const HvArgs<T> a) {
     extern __shared__ double red_sm[];  // [nwarps][3][G*CPL]
@@ -260,34 +213,6 @@ __global__ void __launch_bounds__(kThreads) k_hv(const HvArgs<T> a) {
     }
 }
 
-HvTables make_tables(const hphi_ham *ham, int real_dtype) {
-    const hphi_basis *b = ham->basis;
-    HvTables P{};
-    P.desc = ham->desc;
-    P.model = ham->model;
-    P.nlo = ham->nlo;
-    P.ngroups = ham->host.ngroups;
-    P.n = ham->host.n;
-    P.nh = ham->nh;
-    P.L = ham->L;
-    P.ddn = ham->host.ddn;
-    P.jb = b->sp[0].jb;
-    P.loff = b->sp[0].loff;
-    P.lstate = b->sp[0].lstate;
-    P.states_up = b->sp[0].states;
-    P.states_dn = b->sp[1].states;
-    P.dlow = real_dtype == HPHI_F64 ? (const void *)ham->dlow_d : (const void *)ham->dlow_f;
-    P.ll_cnt = ham->ll_cnt;
-    P.ll_tgt = ham->ll_tgt;
-    P.ll_cf = ham->ll_cf;
-    P.flipq = ham->flipq;
-    P.up_cnt = ham->up_cnt;
-    P.up_tgt = ham->up_tgt;
-    P.up_cf = ham->up_cf;
-    P.aup = ham->aup;
-    return P;
-}
-
 template <typename T, int G, int CPL>
 int grid_for(hphi_ctx *ctx, int64_t nh, bool red) {
     static int occ[64] = {0};
@@ -344,18 +269,70 @@ int dispatch(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, bool pair_ok, boo
 
 template <typename T>
 int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
+    const bool same_ld = L.ldx == L.ldy && (!L.v || L.ldv == L.ldx);
+    int red_mode = -1;
+    if (!L.red[0] && !L.red[1] && !L.red[2]) red_mode = 0;
+    else if (L.red[0] == R_XO && !L.red[1] && !L.red[2]) red_mode = 1;
+    else if (L.red[0] == R_XHX && L.red[1] == R_HXHX && L.red[2] == R_XX) red_mode = 2;
+    else if (L.red[0] == R_OO && !L.red[1] && !L.red[2]) red_mode = 3;
+    constexpr int WIDE = std::is_same<T, float>::value ? 8 : 4;
+    auto aligned = [](const void *p, size_t b) { return p == nullptr || (uintptr_t)p % b == 0; };
     int c0 = 0;
     int64_t part_off = 0;
     L.nslice = 0;
     while (c0 < L.ncol) {
-        int nc = L.ncol - c0 < 32 ? L.ncol - c0 : 32;
+        const int rem = L.ncol - c0;
+        const T *xs = (const T *)L.x + c0;
+        T *ys = (T *)L.y + c0;
+        const T *vs = L.v ? (const T *)L.v + c0 : nullptr;
+        // spin models: the on-the-fly-rank kernel for unit / pair / 32-wide rows
+        int fG = 0, fcpl = 0;
+        // variant -1 (automatic): on-the-fly ranks for 32-wide rows, lists for unit / pair rows
+        const int variant = ham->tune_variant >= 0 ? ham->tune_variant : (L.ldx == 32 ? 1 : 0);
+        const bool fly_ok = variant == 1 && ham->host.n_ll <= 128 &&
+                            (ham->model == HPHI_SPIN_HALF_GC || (ham->model == HPHI_SPIN_HALF && ham->ja16));
+        if (same_ld && red_mode >= 0 && fly_ok && (double)ham->D * (double)L.ldx < 4294967296.0) {
+            if (L.ldx == 1) {
+                fG = 1;
+                fcpl = 1;
+            } else if (L.ldx == 2 && rem >= 2 && aligned(xs, 2 * sizeof(T)) && aligned(ys, 2 * sizeof(T)) &&
+                       aligned(vs, 2 * sizeof(T))) {
+                fG = 1;
+                fcpl = 2;
+            } else if (L.ldx == 32 && c0 == 0 && L.ncol == 32 && aligned(xs, 16) && aligned(ys, 16) &&
+                       aligned(vs, 16)) {
+                fG = std::is_same<T, float>::value ? 8 : 16;
+                fcpl = std::is_same<T, float>::value ? 4 : 2;
+            }
+        }
+        // the lean kernel covers unit / pair / 32-wide rows; the rest goes generic
+        int cpl = 0, ldc = -1;
+        // the lean kernel addresses elements with 32-bit offsets
+        const bool off32 = (double)ham->D * (double)L.ldx < 4294967296.0;
+        // Hubbard: the generic kernel measured fastest; the lean one only on request
+        const bool lean_ok = ham->model != HPHI_HUBBARD || ham->tune_variant == 0;
+        if (same_ld && red_mode >= 0 && off32 && lean_ok && !fG) {
+            const size_t vb = WIDE * sizeof(T) >= 16 ? 16 : WIDE * sizeof(T);
+            if (L.ldx == 1) {
+                cpl = 1;
+                ldc = 1;
+            } else if (L.ldx == 2 && rem >= 2 && aligned(xs, 2 * sizeof(T)) && aligned(ys, 2 * sizeof(T)) &&
+                       aligned(vs, 2 * sizeof(T))) {
+                cpl = 2;
+                ldc = 2;
+            } else if (L.ldx == 32 && rem >= WIDE && aligned(xs, vb) && aligned(ys, vb) && aligned(vs, vb)) {
+                cpl = WIDE;
+                ldc = 32;
+            }
+        }
+        const int nc = fG ? fG * fcpl : (cpl ? cpl : (rem < 32 ? rem : 32));
         HvArgs<T> a;
         a.P = make_tables(ham, L.dtype_real);
-        a.x = (const T *)L.x + c0;
+        a.x = xs;
         a.ldx = L.ldx;
-        a.y = (T *)L.y + c0;
+        a.y = ys;
         a.ldy = L.ldy;
-        a.v = L.v ? (const T *)L.v + c0 : nullptr;
+        a.v = vs;
         a.ldv = L.ldv;
         a.ncol = nc;
         a.beta = L.beta;
@@ -367,18 +344,29 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         a.gamma_dev = L.coef_dev ? L.coef_dev + L.ncol + c0 : nullptr;
         for (int r = 0; r < 3; r++) a.red[r] = L.red[r];
         a.partials = L.partials ? L.partials + part_off : nullptr;
-        bool pair_ok = nc == 2 && (L.ldx % 2 == 0) && (L.ldy % 2 == 0) && (!L.v || L.ldv % 2 == 0) &&
-                       ((uintptr_t)a.x % (2 * sizeof(T)) == 0) && ((uintptr_t)a.y % (2 * sizeof(T)) == 0) &&
-                       (!a.v || (uintptr_t)a.v % (2 * sizeof(T)) == 0);
-        // 32 columns with 16-byte aligned rows: several rows per warp, vector loads
-        const size_t vb = 16;
-        bool quad_ok = nc == 32 && ((L.ldx * sizeof(T)) % vb == 0) && ((L.ldy * sizeof(T)) % vb == 0) &&
-                       (!L.v || (L.ldv * sizeof(T)) % vb == 0) && ((uintptr_t)a.x % vb == 0) &&
-                       ((uintptr_t)a.y % vb == 0) && (!a.v || (uintptr_t)a.v % vb == 0);
-        int grid = 0;
-        int st = dispatch<T>(ctx, ham, a, pair_ok, quad_ok, &grid);
+        int grid = 0, st;
+        if (fG) {
+            set_traversal(ctx, ham, a.P, (double)nc * sizeof(T) < 4.0 ? 4.0 : (double)nc * sizeof(T));
+            a.P.split = ham->tune_split;
+            st = launch_fly<T>(ctx, ham, a, fG, fcpl, red_mode, &grid);
+        } else if (cpl) {
+            set_traversal(ctx, ham, a.P, (double)cpl * sizeof(T) < 4.0 ? 4.0 : (double)cpl * sizeof(T));
+            a.P.split = ham->tune_split;
+            st = launch_lean<T>(ctx, ham, a, cpl, ldc, red_mode, &grid);
+        } else {
+            bool pair_ok = nc == 2 && (L.ldx % 2 == 0) && (L.ldy % 2 == 0) && (!L.v || L.ldv % 2 == 0) &&
+                           aligned(xs, 2 * sizeof(T)) && aligned(ys, 2 * sizeof(T)) && aligned(vs, 2 * sizeof(T));
+            const size_t vb = 16;
+            bool quad_ok = nc == 32 && ((L.ldx * sizeof(T)) % vb == 0) && ((L.ldy * sizeof(T)) % vb == 0) &&
+                           (!L.v || (L.ldv * sizeof(T)) % vb == 0) && aligned(xs, vb) && aligned(ys, vb) &&
+                           aligned(vs, vb);
+            st = dispatch<T>(ctx, ham, a, pair_ok, quad_ok, &grid);
+        }
         if (st) return st;
-        L.sgrid[L.nslice++] = grid;
+        L.sgrid[L.nslice] = grid;
+        L.sc0[L.nslice] = c0;
+        L.snc[L.nslice] = nc;
+        L.nslice++;
         part_off += (int64_t)grid * 3 * nc;
         c0 += nc;
     }
@@ -407,13 +395,10 @@ size_t hv_partials_size(hphi_ctx *ctx, const hphi_ham *ham, int ncol) {
 
 int reduce_hv(hphi_ctx *ctx, const HvLaunch &L, double *out_dev) {
     int64_t off = 0;
-    int c0 = 0;
     for (int s = 0; s < L.nslice; s++) {
-        int nc = L.ncol - c0 < 32 ? L.ncol - c0 : 32;
-        k_reduce_slice<<<1, 96, 0, ctx->stream>>>(L.partials + off, L.sgrid[s], nc, c0, L.ncol, out_dev);
+        k_reduce_slice<<<1, 96, 0, ctx->stream>>>(L.partials + off, L.sgrid[s], L.snc[s], L.sc0[s], L.ncol, out_dev);
         HPHI_CUDA(ctx, cudaGetLastError());
-        off += (int64_t)L.sgrid[s] * 3 * nc;
-        c0 += nc;
+        off += (int64_t)L.sgrid[s] * 3 * L.snc[s];
     }
     return HPHI_OK;
 }
@@ -424,3 +409,40 @@ int launch_hv(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
 }
 
 }  // namespace hphi
+
+using namespace hphi;
+
+extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
+    if (!ham) return HPHI_E_INVAL;
+    switch (knob) {
+    case HPHI_TUNE_INNER_BITS:
+        if (value < -1 || value > 32) return HPHI_E_INVAL;
+        ham->tune_inner = value;
+        return HPHI_OK;
+    case HPHI_TUNE_SPLIT:
+        if (value < 1 || value > 8) return HPHI_E_INVAL;
+        ham->tune_split = value;
+        return HPHI_OK;
+    case HPHI_TUNE_L2_HINTS:
+        if (value != 0 && value != 1) return HPHI_E_INVAL;
+        ham->tune_hints = value;
+        return HPHI_OK;
+    case HPHI_TUNE_VARIANT:
+        if (value < -1 || value > 1) return HPHI_E_INVAL;
+        ham->tune_variant = value;
+        return HPHI_OK;
+    default:
+        return HPHI_E_INVAL;
+    }
+}
+
+extern "C" int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value) {
+    if (!ham || !value) return HPHI_E_INVAL;
+    switch (knob) {
+    case HPHI_TUNE_INNER_BITS: *value = ham->tune_inner; return HPHI_OK;
+    case HPHI_TUNE_SPLIT: *value = ham->tune_split; return HPHI_OK;
+    case HPHI_TUNE_L2_HINTS: *value = ham->tune_hints; return HPHI_OK;
+    case HPHI_TUNE_VARIANT: *value = ham->tune_variant; return HPHI_OK;
+    default: return HPHI_E_INVAL;
+    }
+}

@@ -39,7 +39,25 @@ struct HvTables {
     const uint32_t *up_tgt;
     const uint16_t *up_cf;
     const double *aup;
+    // packed low-low lists (target | coefficient index << 24), null if unavailable
+    const uint32_t *ll_pk;
+    // traversal of the row blocks: counter bit k -> bit hperm[k] of h; bits of
+    // h in outer_mask are outside the L2-resident subcube of the traversal
+    int use_perm;
+    uint32_t outer_mask;
+    uint8_t hperm[32];
+    int split;   // thread blocks sharing one row block
+    int hints;   // L2 eviction-priority hints on
+    const uint16_t *ja16;  // Lin's ja (16-bit), spin sector
 };
+
+// Row block visited at traversal position c.
+__device__ __forceinline__ int64_t block_of(const HvTables &P, int64_t c) {
+    if (!P.use_perm) return c;
+    int64_t h = 0;
+    for (int k = 0; k < 32 && (c >> k) != 0; k++) h |= ((c >> k) & 1) << P.hperm[k];
+    return h;
+}
 
 template <typename T>
 struct HBlock {
@@ -48,98 +66,143 @@ struct HBlock {
     int valid, nhh, nlh;
     T dh;
     uint64_t hbits;
+    double dh_part[2];
     int64_t hh_delta[kMaxHH];
     T hh_coef[kMaxHH];
     int64_t lh_base[kMaxLH];
     T lh_coef[kMaxLH];
     uint16_t lh_bi[kMaxLH];
     uint8_t lh_b[kMaxLH], lh_need[kMaxLH];
+    uint8_t hh_outer[kMaxHH], lh_outer[kMaxLH];  // target block outside the resident subcube
     double w[kMaxGroups * 8];
     T tab[kMaxGroups][256];
 };
 
-// All threads of the block must call this; it ends with __syncthreads().
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Block set-up, shared by every kernel that walks rows block by block.  All
+// threads of the thread block (>= 64 of them) must call it; it ends with
+// __syncthreads().  Warp 0 resolves the high-high bonds (or the up hops) and
+// warp 1 the mixed bonds, one bond per lane, compacting the off-diagonal ones
+// with ballots; then the diagonal weights and byte tables are built.
 template <typename T>
 __device__ void setup_block(const HvTables &P, int64_t h, HBlock<T> &hb) {
     const HamDesc &D = *P.desc;
-    if (threadIdx.x == 0) {
-        double dh = 0.0;
-        int nhh = 0, nlh = 0;
-        if (P.model == kSpin || P.model == kSpinGC) {
-            int64_t base;
-            int valid = 1;
-            uint32_t cp0, len;
-            if (P.model == kSpin) {
-                uint64_t b = P.jb[h];
-                valid = b != ~0ull;
-                base = (int64_t)b;
-                int p = P.n - __popcll((unsigned long long)h);
-                if (valid) {
-                    cp0 = P.loff[p];
-                    len = P.loff[p + 1] - cp0;
-                } else {
-                    cp0 = 0;
-                    len = 0;
-                }
-            } else {
-                base = h << P.nlo;
-                cp0 = 0;
-                len = 1u << P.nlo;
-            }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const bool spin = P.model != kHubbard;
+    if (warp < 2) {
+        // every participating warp derives the block placement itself
+        int64_t base = 0;
+        uint32_t cp0 = 0, len = 0;
+        int valid = 1;
+        if (P.model == kSpin) {
+            const uint64_t b = P.jb[h];
+            valid = b != ~0ull;
+            base = (int64_t)b;
             if (valid) {
-                for (int k = 0; k < D.n_hh; k++) {
-                    const HHBond &bd = D.hh[k];
-                    int bi = (int)((h >> bd.i) & 1), bj = (int)((h >> bd.j) & 1);
-                    if (bi != bj) {
-                        dh += bd.cz;
-                        if (bd.cxy != 0.0 && nhh < kMaxHH) {
-                            uint64_t h2 = (uint64_t)h ^ ((1ull << bd.i) | (1ull << bd.j));
-                            int64_t b2 = P.model == kSpin ? (int64_t)P.jb[h2] : (int64_t)(h2 << P.nlo);
-                            hb.hh_delta[nhh] = b2 - base;
-                            hb.hh_coef[nhh] = (T)bd.cxy;
-                            nhh++;
+                const int p = P.n - __popcll((unsigned long long)h);
+                cp0 = P.loff[p];
+                len = P.loff[p + 1] - cp0;
+            }
+        } else if (P.model == kSpinGC) {
+            base = h << P.nlo;
+            len = 1u << P.nlo;
+        } else {
+            base = h * P.ddn;
+            len = (uint32_t)P.ddn;
+        }
+        double dpart = 0.0;
+        if (warp == 0) {
+            int nhh = 0;
+            if (spin && valid) {
+                for (int k0 = 0; k0 < D.n_hh; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool off = false;
+                    int64_t delta = 0;
+                    double cxy = 0.0;
+                    if (k < D.n_hh) {
+                        const HHBond &bd = D.hh[k];
+                        const bool differ = ((h >> bd.i) & 1) != ((h >> bd.j) & 1);
+                        if (differ) {
+                            dpart += bd.cz;
+                            off = bd.cxy != 0.0;
+                            if (off) {
+                                const uint64_t h2 = (uint64_t)h ^ ((1ull << bd.i) | (1ull << bd.j));
+                                delta = (P.model == kSpin ? (int64_t)P.jb[h2] : (int64_t)(h2 << P.nlo)) - base;
+                                cxy = bd.cxy;
+                            }
                         }
                     }
-                }
-                for (int k = 0; k < D.n_lh; k++) {
-                    const LHBond &bd = D.lh[k];
-                    int ha = (int)((h >> bd.a) & 1);
-                    dh += bd.cz * ha;
-                    if (bd.cxy != 0.0 && nlh < kMaxLH) {
-                        uint64_t h2 = (uint64_t)h ^ (1ull << bd.a);
-                        int64_t b2 = P.model == kSpin ? (int64_t)P.jb[h2] : (int64_t)(h2 << P.nlo);
-                        hb.lh_base[nlh] = b2;
-                        hb.lh_coef[nlh] = (T)bd.cxy;
-                        hb.lh_b[nlh] = (uint8_t)bd.b;
-                        hb.lh_need[nlh] = (uint8_t)(1 - ha);
-                        hb.lh_bi[nlh] = (uint16_t)bd.bi;
-                        nlh++;
+                    const unsigned m = __ballot_sync(0xffffffffu, off);
+                    const int pos = nhh + __popc(m & lt);
+                    if (off && pos < kMaxHH) {
+                        const HHBond &bd = D.hh[k];
+                        hb.hh_delta[pos] = delta;
+                        hb.hh_coef[pos] = (T)cxy;
+                        hb.hh_outer[pos] = (uint8_t)((P.outer_mask >> bd.i) & 1 || (P.outer_mask >> bd.j) & 1);
                     }
+                    nhh += __popc(m);
+                }
+            } else if (!spin) {
+                const int c = P.up_cnt[h];
+                for (int e = lane; e < c && e < kMaxHH; e += 32) {
+                    const int64_t h2 = P.up_tgt[(int64_t)e * P.nh + h];
+                    hb.hh_delta[e] = (h2 - h) * P.ddn;
+                    hb.hh_coef[e] = (T)D.coef[P.up_cf[(int64_t)e * P.nh + h]];
+                    hb.hh_outer[e] = 0;
+                }
+                nhh = c;
+                if (lane == 0) dpart = P.aup[h];
+            }
+            dpart = warp_sum_d(dpart);
+            if (lane == 0) {
+                hb.nhh = nhh < kMaxHH ? nhh : kMaxHH;
+                hb.dh_part[0] = dpart;
+                hb.base = base;
+                hb.cp0 = cp0;
+                hb.len = valid ? len : 0;
+                hb.valid = valid;
+                hb.hbits = spin ? (uint64_t)h : (uint64_t)P.states_up[h];
+            }
+        } else {
+            int nlh = 0;
+            if (spin && valid) {
+                for (int k0 = 0; k0 < D.n_lh; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool keep = false;
+                    if (k < D.n_lh) {
+                        const LHBond &bd = D.lh[k];
+                        const int ha = (int)((h >> bd.a) & 1);
+                        dpart += bd.cz * ha;
+                        keep = bd.cxy != 0.0;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    const int pos = nlh + __popc(m & lt);
+                    if (keep && pos < kMaxLH) {
+                        const LHBond &bd = D.lh[k];
+                        const int ha = (int)((h >> bd.a) & 1);
+                        const uint64_t h2 = (uint64_t)h ^ (1ull << bd.a);
+                        hb.lh_base[pos] = P.model == kSpin ? (int64_t)P.jb[h2] : (int64_t)(h2 << P.nlo);
+                        hb.lh_coef[pos] = (T)bd.cxy;
+                        hb.lh_b[pos] = (uint8_t)bd.b;
+                        hb.lh_need[pos] = (uint8_t)(1 - ha);
+                        hb.lh_bi[pos] = (uint16_t)bd.bi;
+                        hb.lh_outer[pos] = (uint8_t)((P.outer_mask >> bd.a) & 1);
+                    }
+                    nlh += __popc(m);
                 }
             }
-            hb.base = base;
-            hb.cp0 = cp0;
-            hb.len = len;
-            hb.valid = valid;
-            hb.hbits = (uint64_t)h;
-        } else {
-            hb.base = h * P.ddn;
-            hb.cp0 = 0;
-            hb.len = (uint32_t)P.ddn;
-            hb.valid = 1;
-            hb.hbits = P.states_up[h];
-            dh = P.aup[h];
-            int c = P.up_cnt[h];
-            for (int e = 0; e < c && nhh < kMaxHH; e++) {
-                int64_t h2 = P.up_tgt[(int64_t)e * P.nh + h];
-                hb.hh_delta[nhh] = (h2 - h) * P.ddn;
-                hb.hh_coef[nhh] = (T)D.coef[P.up_cf[(int64_t)e * P.nh + h]];
-                nhh++;
+            dpart = warp_sum_d(dpart);
+            if (lane == 0) {
+                hb.nlh = nlh < kMaxLH ? nlh : kMaxLH;
+                hb.dh_part[1] = dpart;
             }
         }
-        hb.dh = (T)dh;
-        hb.nhh = nhh;
-        hb.nlh = nlh;
     }
     __syncthreads();
     // weights of the mixed diagonal part, one per low bit / down site:
@@ -147,14 +210,14 @@ __device__ void setup_block(const HvTables &P, int64_t h, HBlock<T> &hb) {
     //   Hubbard: w_j = U_j n_j,up + sum_{V terms with j} V n_other,up
     const int nbits = P.ngroups * 8;
     if ((int)threadIdx.x < nbits) {
-        int b = threadIdx.x;
+        const int b = threadIdx.x;
         double w = 0.0;
         if (hb.valid) {
-            if (P.model == kSpin || P.model == kSpinGC) {
+            if (spin) {
                 for (int k = 0; k < D.n_lh; k++)
                     if (D.lh[k].b == b) w += D.lh[k].cz * (1 - 2 * (int)((hb.hbits >> D.lh[k].a) & 1));
             } else if (b < D.N) {
-                uint64_t su = hb.hbits;
+                const uint64_t su = hb.hbits;
                 w = D.U[b] * (double)((su >> b) & 1);
                 for (int k = 0; k < D.n_v; k++) {
                     if (D.v[k].j == b) w += D.v[k].v * (double)((su >> D.v[k].i) & 1);
@@ -164,6 +227,7 @@ __device__ void setup_block(const HvTables &P, int64_t h, HBlock<T> &hb) {
         }
         hb.w[b] = w;
     }
+    if (threadIdx.x == 32 * 2) hb.dh = (T)(hb.dh_part[0] + hb.dh_part[1]);
     __syncthreads();
     if (threadIdx.x < 256 && hb.valid) {
         for (int g = 0; g < P.ngroups; g++) {

@@ -206,6 +206,51 @@ __global__ void k_copy(int64_t n, int nr, const T *x, int64_t ldx, T *y, int64_t
     }
 }
 
+// c[j] partials = sum over this block's rows of V[j][r] * w[r], j in a chunk of
+// 8 stored vectors (grid.y walks the chunks).  V holds nv vectors of length n,
+// vector j at V + j * n.  Fixed grid and order: deterministic.
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_mdot(int64_t n, int nv, const T *__restrict__ V, const T *__restrict__ w,
+                                              double *partials) {
+    constexpr int J = 8;
+    __shared__ double sm[kVT / 32][J];
+    const int j0 = blockIdx.y * J;
+    Acc<T> s[J];
+    for (int64_t r = blockIdx.x * (int64_t)kVT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kVT) {
+        const T wv = w[r];
+#pragma unroll
+        for (int j = 0; j < J; j++)
+            if (j0 + j < nv) s[j].add(V[(int64_t)(j0 + j) * n + r], wv);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+        double v = s[j].value();
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sm[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < J && j0 + (int)threadIdx.x < nv) {
+        double acc = 0.0;
+        for (int w2 = 0; w2 < kVT / 32; w2++) acc += sm[w2][threadIdx.x];
+        partials[(int64_t)blockIdx.x * nv + j0 + threadIdx.x] = acc;
+    }
+}
+
+// w[r] -= sum_j c[j] V[j][r] (c on the device, FP64; accumulated in T)
+template <typename T>
+__global__ void k_maxpy(int64_t n, int nv, const T *__restrict__ V, const double *__restrict__ c, T *w) {
+    __shared__ T cs[1024];
+    for (int j = threadIdx.x; j < nv && j < 1024; j += blockDim.x) cs[j] = (T)c[j];
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        T acc = (T)0;
+        for (int j = 0; j < nv; j++) acc = fma(cs[j], V[(int64_t)j * n + r], acc);
+        w[r] -= acc;
+    }
+}
+
 int vec_grid(hphi_ctx *ctx, int64_t n, int tpr) {
     int64_t rows_per_block = kVT / tpr;
     int64_t g = (n + rows_per_block - 1) / rows_per_block;
@@ -286,6 +331,40 @@ int launch_lincomb(hphi_ctx *ctx, LinComb &L) {
         else HPHI_LC(float, 8);
     }
 #undef HPHI_LC
+    prof_end(ctx, slot);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const void *w, double *out_dev) {
+    int64_t gx = (n + kVT - 1) / kVT;
+    const int64_t cap = (int64_t)ctx->sm_count * 4;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    const int gy = (nv + 7) / 8;
+    int st = ensure_partials(ctx, (size_t)gx * nv);
+    if (st) return st;
+    const int slot = prof_begin(ctx, PROF_VEC);
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    if (real_dtype == HPHI_F64)
+        k_mdot<double><<<grid, kVT, 0, ctx->stream>>>(n, nv, (const double *)V, (const double *)w, ctx->partials);
+    else
+        k_mdot<float><<<grid, kVT, 0, ctx->stream>>>(n, nv, (const float *)V, (const float *)w, ctx->partials);
+    prof_end(ctx, slot);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return reduce_partials(ctx, ctx->partials, (int)gx, nv, out_dev);
+}
+
+int launch_maxpy(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const double *c_dev, void *w) {
+    if (nv > 1024) return set_err(ctx, HPHI_E_INVAL, "at most 1024 stored vectors");
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)ctx->sm_count * 8) g = (int64_t)ctx->sm_count * 8;
+    if (g < 1) g = 1;
+    const int slot = prof_begin(ctx, PROF_VEC);
+    if (real_dtype == HPHI_F64)
+        k_maxpy<double><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nv, (const double *)V, c_dev, (double *)w);
+    else
+        k_maxpy<float><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nv, (const float *)V, c_dev, (float *)w);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;

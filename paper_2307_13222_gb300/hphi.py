@@ -35,7 +35,8 @@ class _Term(C.Structure):
 
 
 class _LanczosOpts(C.Structure):
-    _fields_ = [("max_steps", C.c_int), ("tol", C.c_double), ("dtype", C.c_int), ("check_every", C.c_int)]
+    _fields_ = [("max_steps", C.c_int), ("tol", C.c_double), ("dtype", C.c_int), ("check_every", C.c_int),
+                ("reorth", C.c_int)]
 
 
 class _LanczosResult(C.Structure):
@@ -63,6 +64,8 @@ _SIGS = {
     "hphi_build_hamiltonian": (i32, [vp, vp, vp, i32, C.POINTER(vp)]),
     "hphi_ham_destroy": (None, [vp]),
     "hphi_ham_dim": (i64, [vp]),
+    "hphi_ham_set_tuning": (i32, [vp, i32, i32]),
+    "hphi_ham_get_tuning": (i32, [vp, i32, C.POINTER(i32)]),
     "hphi_apply_H": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, dbl, dbl]),
     "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
     "hphi_dot": (i32, [vp, i32, i64, i32, vp, i64, vp, i64, vp]),
@@ -228,6 +231,21 @@ class Hamiltonian:
         self.h = h
         self.dim = int(ctx.lib.hphi_ham_dim(h))
 
+    TUNE = {"inner_bits": 0, "split": 1, "l2_hints": 2, "variant": 3}
+
+    def set_tuning(self, **knobs):
+        """Launch knobs of the H*x kernel: inner_bits, split, l2_hints, variant."""
+        for k, v in knobs.items():
+            self.ctx.check(self.ctx.lib.hphi_ham_set_tuning(self.h, self.TUNE[k], int(v)))
+
+    def get_tuning(self):
+        out = {}
+        for k, code in self.TUNE.items():
+            v = C.c_int(0)
+            self.ctx.check(self.ctx.lib.hphi_ham_get_tuning(self.h, code, C.byref(v)))
+            out[k] = v.value
+        return out
+
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.hphi_ham_destroy(self.h)
@@ -319,11 +337,12 @@ def hphi_random_vector(ctx: Context, x, seed: int):
     return x
 
 
-def hphi_lanczos(ham: Hamiltonian, v0, max_steps: int, tol: float, check_every: int = 1, gs_out=None):
+def hphi_lanczos(ham: Hamiltonian, v0, max_steps: int, tol: float, check_every: int = 1, gs_out=None,
+                 reorth: bool = False):
     """Lanczos from v0 (F64 or F32 CUDA vector). Returns a dict; NOTCONV is reported, not raised."""
     ctx = ham.ctx
     dc = _dtype_code(v0)
-    opts = _LanczosOpts(max_steps, tol, dc, check_every)
+    opts = _LanczosOpts(max_steps, tol, dc, check_every, 1 if reorth else 0)
     res = _LanczosResult()
     alpha = np.zeros(max_steps)
     beta = np.zeros(max_steps + 1)

@@ -176,3 +176,22 @@ def test_rrg26_block32_full_size_sampled(dtype):
     rng = np.random.default_rng(10)
     rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 200)])
     assert _sampled_rows(m, h, dtype, 32, rows, 44) < (1e-15 if dtype == torch.float64 else 1e-6)
+
+
+@pytest.mark.parametrize("variant,split,hints,inner", [(-1, 1, 1, -1), (0, 1, 1, -1), (1, 1, 1, -1),
+                                                       (0, 3, 0, 2), (1, 2, 0, 1), (1, 4, 1, 0), (-1, 8, 1, 32)])
+@pytest.mark.parametrize("shape", ["sector", "full", "hubbard"])
+@pytest.mark.parametrize("nvec", [1, 2, 32])
+def test_kernel_variants_and_knobs(variant, split, hints, inner, shape, nvec):
+    """Every H*x kernel (generic, table-driven, on-the-fly ranks) and launch knob
+    gives the oracle's result; the reductions are checked through Lanczos/TPQ."""
+    if shape == "sector":
+        m, b, h = pair("SPIN_HALF", 14, 7, 0, heisenberg_terms(square(7, 2), 1.0))
+    elif shape == "full":
+        bonds = random_regular_graph(14, 3, 9)
+        m, b, h = pair("SPIN_HALF_GC", 14, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 3)))
+    else:
+        m, b, h = pair("HUBBARD", 8, 4, 3, hubbard_terms(8, chain(8), t=1.0, U=4.0, V=0.3))
+    h.set_tuning(variant=variant, split=split, l2_hints=hints, inner_bits=inner)
+    for dtype in (torch.float64, torch.float32):
+        _check(m, h, dtype, nvec, alpha=0.9, beta=0.0 if nvec == 32 else 0.4, seed=nvec + split)

@@ -74,3 +74,46 @@ def test_deterministic_bitwise():
     r1 = hphi.hphi_lanczos(h, v0, 40, 0.0, check_every=40)
     r2 = hphi.hphi_lanczos(h, v0, 40, 0.0, check_every=7)
     assert np.array_equal(r1["alpha"], r2["alpha"]) and np.array_equal(r1["beta"], r2["beta"])
+
+
+def test_reorth_reproduces_full_spectrum():
+    """With full reorthogonalisation, D Lanczos steps on a non-degenerate D=70
+    sector give T_D whose eigenvalues are the whole dense spectrum."""
+    N = 8
+    terms = heisenberg_terms(chain(N), uniform_couplings(N, 0.5, 1.5, 21))
+    m, b, h = pair("SPIN_HALF", N, N // 2, 0, terms)
+    w = np.linalg.eigvalsh(O.dense_matrix(m))
+    assert np.min(np.diff(w)) > 1e-6  # non-degenerate
+    r = hphi.hphi_lanczos(h, torch.from_numpy(random_vectors(m.dim, 1, 4)[:, 0]).cuda(), m.dim, 0.0,
+                          check_every=m.dim, reorth=True)
+    k = r["steps"]
+    assert k >= m.dim - 1
+    ev, _ = hphi.hphi_tridiag_eigen(r["alpha"], np.concatenate([[0.0], r["beta"][:k - 1]]))
+    assert np.allclose(np.sort(ev)[:len(w)], w[:len(ev)], atol=1e-9)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 1e-6)])
+def test_reorth_hubbard_and_chain_vs_oracle(dtype, tol):
+    for model, N, nu, nd, terms in (("HUBBARD", 8, 4, 4, hubbard_terms(8, chain(8), t=1.0, U=8.0)),
+                                    ("SPIN_HALF", 16, 8, 0, heisenberg_terms(chain(16), 1.0))):
+        m, b, h = pair(model, N, nu, nd, terms)
+        v0 = random_vectors(m.dim, 1, 6)[:, 0]
+        ro = m.lanczos(v0, 300, 1e-12)
+        gs = torch.empty(m.dim, dtype=dtype, device="cuda")
+        r = hphi.hphi_lanczos(h, torch.from_numpy(v0).to(dtype).cuda(), 300, 1e-10 if dtype == torch.float64 else 1e-6,
+                              gs_out=gs, reorth=True)
+        assert r["converged"], r
+        assert abs(r["e0"] - ro["e0"]) <= tol * abs(ro["e0"]), (model, r["e0"], ro["e0"])
+        assert r["resid"] < (1e-8 if dtype == torch.float64 else 1e-3) * max(1.0, abs(r["e0"]))
+
+
+def test_reorth_storage_beyond_device_memory_is_nomem():
+    """(max_steps + 1) stored vectors that cannot fit the device: NOMEM, no crash."""
+    m, b, h = pair("SPIN_HALF", 28, 14, 0, heisenberg_terms(chain(28)))   # 40,116,600 rows
+    v0 = torch.zeros(m.dim, dtype=torch.float64, device="cuda")
+    v0[0] = 1.0
+    free, total = torch.cuda.mem_get_info()
+    steps = int(2 * total // (m.dim * 8))  # twice the device memory
+    with pytest.raises(hphi.HphiError) as ei:
+        hphi.hphi_lanczos(h, v0, steps, 1e-10, reorth=True)
+    assert ei.value.code == -2
