@@ -145,6 +145,21 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The job's time is its slowest replica's: MAX of the per-rank times."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbps(world, bytes_per_rank, ms):
+    """Whole-job throughput: every replica moves the same bytes in parallel."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def lanczos_steps(ham, v0, steps):
     from paper_2307_13222_gb300 import hphi
     return hphi.hphi_lanczos(ham, v0, steps, 0.0, check_every=steps)
@@ -178,14 +193,10 @@ def measure_dtype(ctx, ham, dim, dtype_name, K, W, dist, world):
     hv_n, hv_ms = ctx.profile_read(0)
     vec_n, vec_ms = ctx.profile_read(1)
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     del v0
     torch.cuda.empty_cache()
-    total_bytes = world * K * 2.0 * es * dim
-    return dict(ms=ms, wall_s=wall, value=total_bytes / (ms * 1e-3) / 1e9, hv_launches=hv_n, hv_ms=hv_ms,
+    return dict(ms=ms, wall_s=wall, value=job_gbps(world, K * 2.0 * es * dim, ms), hv_launches=hv_n, hv_ms=hv_ms,
                 vec_launches=vec_n, vec_ms=vec_ms, e0=r["e0"], steps=r["steps"], es=es)
 
 

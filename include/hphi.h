@@ -163,6 +163,10 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         ranks computed on the fly from Lin's ja table, 0 =
  *                         precomputed neighbour lists (also enables the
  *                         one-thread-per-row kernel for Hubbard)
+ *   HPHI_TUNE_COOP        32-column rows: 1 = the lanes of a row split the
+ *                         bond evaluation and share targets, 0 = every lane
+ *                         evaluates every bond, -1 = 1 for FP32 and 0 for
+ *                         FP64 data (default)
  * Results do not depend on the knobs except through summation order of the
  * reductions (still deterministic for fixed knobs).  HPHI_E_INVAL for an
  * unknown knob or value. */
@@ -170,6 +174,7 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
 #define HPHI_TUNE_SPLIT 1
 #define HPHI_TUNE_L2_HINTS 2
 #define HPHI_TUNE_VARIANT 3
+#define HPHI_TUNE_COOP 4
 HPHI_API int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value);
 HPHI_API int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value);
 

@@ -156,6 +156,7 @@ struct hphi_ham {
     int tune_split = 1;
     int tune_hints = 1;
     int tune_variant = -1;       // -1: automatic, 1: on-the-fly ranks (spin), 0: table-driven
+    int tune_coop = -1;          // wide rows: lanes of a row share the bond work (-1: FP32 only)
 };
 
 namespace hphi {

@@ -431,6 +431,10 @@ extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
         if (value < -1 || value > 1) return HPHI_E_INVAL;
         ham->tune_variant = value;
         return HPHI_OK;
+    case HPHI_TUNE_COOP:
+        if (value < -1 || value > 1) return HPHI_E_INVAL;
+        ham->tune_coop = value;
+        return HPHI_OK;
     default:
         return HPHI_E_INVAL;
     }
@@ -443,6 +447,7 @@ extern "C" int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value) {
     case HPHI_TUNE_SPLIT: *value = ham->tune_split; return HPHI_OK;
     case HPHI_TUNE_L2_HINTS: *value = ham->tune_hints; return HPHI_OK;
     case HPHI_TUNE_VARIANT: *value = ham->tune_variant; return HPHI_OK;
+    case HPHI_TUNE_COOP: *value = ham->tune_coop; return HPHI_OK;
     default: return HPHI_E_INVAL;
     }
 }

@@ -1,0 +1,62 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks (replicas) agree
+on the job time (max over ranks) and the whole-job throughput; the reference
+arm does its work on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms_local = [12.5, 30.0, 7.0, 21.0][rank]
+        dist.barrier()
+        ms = bench.max_over_ranks(ms_local, dist, device="cpu")
+        value = bench.job_gbps(world, 1e9, ms)
+        with open(os.path.join(out, f"r{rank}.txt"), "w") as f:
+            f.write(f"{ms} {value}")
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_max_over_ranks_and_job_value(tmp_path, world):
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    want_ms = max([12.5, 30.0, 7.0, 21.0][:world])
+    for r in range(world):
+        ms, value = map(float, (tmp_path / f"r{r}.txt").read_text().split())
+        assert ms == want_ms
+        assert value == pytest.approx(world * 1e9 / (want_ms * 1e-3) / 1e9)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.25, None) == 3.25
+    assert bench.job_gbps(1, 2e9, 1000.0) == pytest.approx(2.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        steps, warmup, gpus = 2, 3, 2
+    assert bench.run_reference(A()) == 0
+    assert capsys.readouterr().out == ""

@@ -195,3 +195,22 @@ def test_kernel_variants_and_knobs(variant, split, hints, inner, shape, nvec):
     h.set_tuning(variant=variant, split=split, l2_hints=hints, inner_bits=inner)
     for dtype in (torch.float64, torch.float32):
         _check(m, h, dtype, nvec, alpha=0.9, beta=0.0 if nvec == 32 else 0.4, seed=nvec + split)
+
+
+@pytest.mark.parametrize("coop", [-1, 0, 1])
+@pytest.mark.parametrize("split", [1, 3])
+@pytest.mark.parametrize("shape", ["sector", "full"])
+def test_wide_rows_cooperative_knob(coop, split, shape):
+    """32-column rows: bond work shared by the lanes of a row (coop=1) or
+    repeated per lane (coop=0) gives the oracle's result, with and without an
+    accumulate term."""
+    if shape == "sector":
+        m, b, h = pair("SPIN_HALF", 16, 8, 0, heisenberg_terms(square(4, 4), 1.0))
+    else:
+        bonds = random_regular_graph(16, 3, 12)
+        m, b, h = pair("SPIN_HALF_GC", 16, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 5)))
+    h.set_tuning(variant=1, coop=coop, split=split)
+    assert h.get_tuning()["coop"] == coop
+    for dtype in (torch.float64, torch.float32):
+        _check(m, h, dtype, 32, alpha=1.1, beta=0.0, seed=20 + split)
+        _check(m, h, dtype, 32, alpha=-0.6, beta=0.25, seed=21 + split)

@@ -47,3 +47,23 @@ def test_tpq_sector_model():
         e, h2, logd = hphi.hphi_tpq_step(h, Vg, 0.05, 6, norm2)
         eo, h2o, do = m.tpq_step(Vo, 0.05, 6)
     assert np.allclose(e, eo, rtol=1e-12) and np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("coop", [-1, 0, 1])
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_tpq_block_of_16_complex_vectors(coop, dtype):
+    """16 complex vectors = 32-column rows, the fused <x,Hx>, |Hx|^2, |x|^2
+    reductions of the wide-row kernel in both bond-sharing modes."""
+    m, b, h = pair("SPIN_HALF_GC", 12, 0, 0, _model(12, 5))
+    h.set_tuning(variant=1, coop=coop)
+    V0 = random_vectors(m.dim, 16, 23, complex_=True)
+    Vg = torch.from_numpy(V0).to(dtype).cuda().contiguous()
+    Vo = Vg.cpu().numpy().astype(np.complex128).copy()
+    norm2 = np.zeros(16)
+    tol = 1e-11 if dtype == torch.complex128 else 2e-5
+    for step in range(12):
+        e, h2, logd = hphi.hphi_tpq_step(h, Vg, 0.05, 6, norm2)
+        eo, h2o, do = m.tpq_step(Vo, 0.05, 6)
+        assert np.allclose(e, eo, rtol=tol, atol=tol), (step, e, eo)
+        assert np.allclose(h2, h2o, rtol=tol), step
+        assert np.allclose(logd, np.log(do), rtol=tol, atol=tol), step
