@@ -840,3 +840,32 @@ int orc_tpq_step(const orc_model *m, int nvec, int ncomp, double *V, double dtau
     free(acc);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Excitation operator of the dynamical structure factor (Sec. 3.2):         */
+/*   y = sum_l A_l S^z_l x,  A_l complex (A_l = e^{i q l} is the paper's      */
+/* O_spin at wave number q).  S^z_l = n_l - 1/2 for spin-1/2 (bit l of the    */
+/* spin string) and (n_{l up} - n_{l dn}) / 2 for Hubbard.  x is one real     */
+/* vector of length D; the result is y_re + i y_im.                           */
+/* ------------------------------------------------------------------------- */
+int orc_apply_sz_sum(const orc_model *m, const double *a_re, const double *a_im, const double *x, double *y_re,
+                     double *y_im)
+{
+    for (int64_t r = 0; r < m->D; r++) {
+        uint64_t su, sd;
+        orc_row_state(m, r, &su, &sd);
+        double f_re = 0.0, f_im = 0.0;
+        for (int l = 0; l < m->N; l++) {
+            double sz;
+            if (m->model == ORC_HUBBARD)
+                sz = 0.5 * ((double)((su >> l) & 1u) - (double)((sd >> l) & 1u));
+            else
+                sz = (double)((su >> l) & 1u) - 0.5;
+            f_re += a_re[l] * sz;
+            f_im += a_im[l] * sz;
+        }
+        y_re[r] = f_re * x[r];
+        y_im[r] = f_im * x[r];
+    }
+    return ORC_OK;
+}

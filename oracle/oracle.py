@@ -75,6 +75,7 @@ def _L():
             "orc_lanczos": (i32, [vp, vp, i32, dbl, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), vp]),
             "orc_tpq_step": (i32, [vp, i32, i32, vp, dbl, i32, vp, vp, vp]),
+            "orc_apply_sz_sum": (i32, [vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -226,6 +227,19 @@ class Model:
             raise ValueError("lanczos failed")
         k = steps.value
         return dict(status=st, steps=k, e0=e0.value, resid=res.value, alpha=alpha[:k], beta=beta[:k + 1], gs=gs)
+
+    def sz_sum(self, x: np.ndarray, A) -> np.ndarray:
+        """sum_l A_l S^z_l x for one real vector x and complex weights A[N]."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        assert x.size == self.dim
+        A = np.asarray(A, dtype=np.complex128).reshape(-1)
+        assert A.size == self.n_sites
+        are, aim = np.ascontiguousarray(A.real), np.ascontiguousarray(A.imag)
+        yr, yi = np.zeros(self.dim), np.zeros(self.dim)
+        st = _L().orc_apply_sz_sum(self._h, _ptr(are), _ptr(aim), _ptr(x), _ptr(yr), _ptr(yi))
+        if st != 0:
+            raise ValueError("sz_sum failed")
+        return yr + 1j * yi
 
     def tpq_step(self, V: np.ndarray, dtau: float, nmax: int):
         """One cTPQ step in place on V ([D][nvec] real or complex). Returns e, h2, d."""
