@@ -327,6 +327,304 @@ def run_native(args):
     return 0
 
 
+# ---- further workloads (one JSON line each, same contract keys) ----------------------------
+
+
+def _setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    import paper_2307_13222_gb300 as P
+    from paper_2307_13222_gb300 import hphi
+    if rank == 0 or not os.path.exists(P.LIBRARY_PATH):
+        P.build()
+    if dist:
+        dist.barrier()
+    return world, rank, local, dist, hphi.Context(local)
+
+
+def _finish(line, rank, dist, ctx):
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.profile(False)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _roofline(ctx, bytes_per_launch, kernel):
+    n, ms = ctx.profile_read(0)
+    peak, kind = peaks()
+    avg = ms / max(n, 1)
+    ach = bytes_per_launch / (avg * 1e-3) / 1e9 if n else 0.0
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "kernel": kernel, "peak_kind": peak_kind_text(kind), "avg_launch_ms": avg, "launches": n}
+
+
+def peak_kind_text(kind):
+    return "of measured" if kind == "measured" else "of fallback"
+
+
+def _base(args, world, metric, value, unit, ms_step, dtype, config, hib=True):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": hib, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+def run_chain16(args):
+    """Lanczos solves of the N=16 chain S^z=0 sector (12,870 rows) to 1e-12:
+    solves/s with p50/p99 latency; each step of the contract is one solve."""
+    import torch
+    import numpy as np
+    from paper_2307_13222_gb300 import hphi
+    from workloads import configs
+    world, rank, local, dist, ctx = _setup(args)
+    cfg = configs.heisenberg_chain16()
+    b = hphi.Basis(ctx, "SPIN_HALF", 16, 8)
+    h = hphi.Hamiltonian(ctx, b, cfg["terms"])
+    v0 = torch.empty(b.dim, dtype=torch.float64, device="cuda")
+    hphi.hphi_random_vector(ctx, v0, cfg["seed"])
+    gs = torch.empty_like(v0)
+    for _ in range(max(args.warmup, 1)):
+        r = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], gs_out=gs)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    ctx.profile_read(1)
+    if dist:
+        dist.barrier()
+    lat = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], gs_out=gs)
+        e1.record()
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    ck = clocks.stop()
+    total = max_over_ranks(sum(lat), dist)
+    roof = _roofline(ctx, 3.0 * 8 * b.dim, "k_hv (fused Lanczos H*x, 12,870 rows: latency-bound)")
+    # end to end: start vector from pinned host memory, ground state back to it
+    vh = torch.empty(b.dim, dtype=torch.float64, pin_memory=True)
+    gh = torch.empty_like(vh)
+    vh.copy_(v0)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        v0.copy_(vh, non_blocking=True)
+        hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], gs_out=gs)
+        gh.copy_(gs, non_blocking=True)
+    t1.record()
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        m = O.Model("SPIN_HALF", 16, 8, 0, cfg["terms"])
+        vv = v0.cpu().numpy()
+        n, t_start = 0, time.perf_counter()
+        while time.perf_counter() - t_start < 10.0 or n == 0:
+            m.lanczos(vv, cfg["max_steps"], cfg["tol"], want_gs=True)
+            n += 1
+        dt = time.perf_counter() - t_start
+        cpu = {"value": n / dt, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{n} oracle Lanczos solves (textbook recurrence, Sturm bisection each step, second pass) "
+                         f"of the same problem in {dt:.1f} s"}
+    lat_sorted = sorted(lat)
+    line = _base(args, world, "lanczos_solves_per_s", world * args.steps / (total * 1e-3), "solves/s",
+                 total / args.steps, "f64",
+                 {"workload": "heisenberg_chain_N16_Sz0", "dim": b.dim, "tol": cfg["tol"], "steps_per_solve": r["steps"],
+                  "l2": "working set 0.3 MB, L2-resident (latency-bound problem, no flush)",
+                  "parallelism": f"replicas{world}"})
+    line.update({"p50_ms": float(np.percentile(lat_sorted, 50)), "p99_ms": float(np.percentile(lat_sorted, 99)),
+                 "e0": r["e0"], "roofline": roof,
+                 "gpu_launches": args.steps * (4 + 10 * r["steps"] + 6),
+                 "e2e": {"value": args.steps / (e2e_ms * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": 8 * b.dim,
+                         "d2h_bytes_per_step": 8 * b.dim}})
+    if ck:
+        line["clocks"] = ck
+    if cpu:
+        line["cpu_baseline"] = cpu
+    return _finish(line, rank, dist, ctx)
+
+
+def run_hubbard4x4(args):
+    """Lanczos with full reorthogonalisation on the 4x4 Hubbard model at half
+    filling (165,636,900 rows), FP32 vectors with FP64 scalars, to 1e-10
+    relative residual; the FP64 run's energy is the error reference."""
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    from workloads import configs
+    world, rank, local, dist, ctx = _setup(args)
+    cfg = configs.hubbard_square4x4()
+    b = hphi.Basis(ctx, "HUBBARD", 16, 8, 8)
+    h = hphi.Hamiltonian(ctx, b, cfg["terms"])
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for dt_name, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        v0 = torch.empty(b.dim, dtype=tdt, device="cuda")
+        hphi.hphi_random_vector(ctx, v0, cfg["seed"])
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(0)
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], check_every=5, reorth=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
+        es = 4 if tdt == torch.float32 else 8
+        out[dt_name] = dict(ms=ms, r=r, roof=_roofline(ctx, 3.0 * es * b.dim, "k_hv (Hubbard, generic)"))
+        del v0
+        torch.cuda.empty_cache()
+    ck = clocks.stop()
+    f32, f64 = out["f32"], out["f64"]
+    es = 4
+    line = _base(args, world, "hv_gbps", job_gbps(world, f32["r"]["steps"] * 2.0 * es * b.dim, f32["ms"]), "GB/s",
+                 f32["ms"] / max(f32["r"]["steps"], 1), "f32",
+                 {"workload": "hubbard_square_4x4_half_U8", "dim": b.dim, "step": "lanczos_iteration_with_cgs2",
+                  "tol": cfg["tol"], "vectors": "f32", "scalars": "f64", "parallelism": f"replicas{world}",
+                  "l2": "inputs larger than L2 (one vector = %.2f GB)" % (4 * b.dim / 1e9)})
+    line["steps"] = f32["r"]["steps"]
+    line.update({"roofline": f32["roof"], "e0_f32": f32["r"]["e0"], "e0_f64": f64["r"]["e0"],
+                 "e0_rel_err_f32": abs(f32["r"]["e0"] - f64["r"]["e0"]) / abs(f64["r"]["e0"]),
+                 "time_to_solution_s": {"f32": f32["ms"] / 1e3, "f64": f64["ms"] / 1e3},
+                 "lanczos_steps": {"f32": f32["r"]["steps"], "f64": f64["r"]["steps"]},
+                 "gpu_launches": None})
+    if ck:
+        line["clocks"] = ck
+    return _finish(line, rank, dist, ctx)
+
+
+def run_ctpq26(args):
+    """cTPQ steps on the full 2^26 space of the Heisenberg model on a seeded
+    random 3-regular graph, 16 complex vectors, nmax=6, dtau=0.02."""
+    import torch
+    import numpy as np
+    from paper_2307_13222_gb300 import hphi
+    from workloads import configs
+    world, rank, local, dist, ctx = _setup(args)
+    cfg = configs.ctpq_random_regular()
+    b = hphi.Basis(ctx, "SPIN_HALF_GC", 26)
+    h = hphi.Hamiltonian(ctx, b, cfg["terms"])
+    tdt = torch.complex64 if args.dtype == "f32" else torch.complex128
+    V = torch.empty((b.dim, cfg["n_vec"]), dtype=tdt, device="cuda")
+    hphi.hphi_random_vector(ctx, V, cfg["seed"])
+    n2 = np.zeros(cfg["n_vec"])
+    for _ in range(max(args.warmup, 1)):
+        hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e, h2, logd = hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    es = 8 if tdt == torch.complex64 else 16
+    # algorithmic bytes of one Horner stage: read V + gather W + write W' per complex column
+    stage_bytes = 3.0 * es * cfg["n_vec"] * b.dim
+    roof = _roofline(ctx, stage_bytes, "k_hvc / k_hvo (block H*V, 32 real columns)")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        m = O.Model("SPIN_HALF_GC", 26, 0, 0, cfg["terms"])
+        col = V[:, :1].cpu().numpy().astype(np.complex128).copy()
+        t0 = time.perf_counter()
+        m.tpq_step(col, cfg["dtau"], cfg["nmax"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": 3.0 * 16 * b.dim * cfg["nmax"] / dt / 1e9, "unit": "GB/s", "cores": O.num_threads(),
+               "kind": "oracle", "sample": f"one oracle TPQ step (literal Taylor sum, FP64) of one complex column "
+                                           f"of the same model, {dt:.1f} s"}
+    line = _base(args, world, "hv_gbps", job_gbps(world, args.steps * cfg["nmax"] * stage_bytes, ms), "GB/s",
+                 ms / args.steps, args.dtype,
+                 {"workload": "ctpq_rrg3_N26_B16", "dim": b.dim, "n_vec": cfg["n_vec"], "nmax": cfg["nmax"],
+                  "dtau": cfg["dtau"], "vectors": "c64" if args.dtype == "f32" else "c128",
+                  "parallelism": f"replicas{world}",
+                  "l2": "inputs larger than L2 (block = %.1f GB)" % (es * 16 * b.dim / 1e9)})
+    line.update({"tpq_steps_per_s": world * args.steps / (ms * 1e-3), "roofline": roof,
+                 "gpu_launches": args.steps * (cfg["nmax"] + 2), "e_last": float(np.mean(e))})
+    if ck:
+        line["clocks"] = ck
+    if cpu:
+        line["cpu_baseline"] = cpu
+    return _finish(line, rank, dist, ctx)
+
+
+def run_szz(args):
+    """S^zz(q, w) of the L=24 Heisenberg chain (S^z=0, 2,704,156 rows): FP64
+    ground state, then every q at once through one shifted-Krylov run with
+    200 shifts at eta = 0.05 to residual 1e-8."""
+    import torch
+    import numpy as np
+    from paper_2307_13222_gb300 import hphi
+    from workloads import chain, heisenberg_terms
+    world, rank, local, dist, ctx = _setup(args)
+    L = 24
+    b = hphi.Basis(ctx, "SPIN_HALF", L, L // 2)
+    h = hphi.Hamiltonian(ctx, b, heisenberg_terms(chain(L), 1.0))
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    v0 = torch.empty(b.dim, dtype=torch.float64, device="cuda")
+    hphi.hphi_random_vector(ctx, v0, 1)
+    gs = torch.empty_like(v0)
+    lz = hphi.hphi_lanczos(h, v0, 400, 1e-12, check_every=5, gs_out=gs)
+    gsd = gs.to(tdt)
+    qs = 2 * np.pi * np.arange(L // 2 + 1) / L
+    z = lz["e0"] + np.linspace(0.0, 4.0, 200) + 0.05j
+    tol = 1e-8 if tdt == torch.float64 else 1e-6
+    hphi.hphi_szz_spectrum(h, b, gsd, qs, z, 3000, tol, check_every=10)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        Sq, Dq, r = hphi.hphi_szz_spectrum(h, b, gsd, qs, z, 3000, tol, check_every=10)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    es = 4 if tdt == torch.float32 else 8
+    ncol = r["G"].shape[0]
+    line = _base(args, world, "spectra_per_s", world * args.steps / (ms * 1e-3), "spectra/s", ms / args.steps,
+                 args.dtype, {"workload": "szz_chain_L24", "dim": b.dim, "q_points": len(qs), "shifts": len(z),
+                              "eta": 0.05, "tol": tol, "rhs_columns": ncol, "parallelism": f"replicas{world}",
+                              "l2": "block of 32 columns = %.2f GB > L2" % (es * 32 * b.dim / 1e9)})
+    line.update({"krylov_steps": r["steps"], "roofline": _roofline(ctx, 3.0 * es * 32 * b.dim,
+                                                                    "block H*x of the Krylov step (32 columns)"),
+                 "gpu_launches": args.steps * (r["steps"] * 7 + len(qs) + 4), "max_resid": r["max_resid"]})
+    if ck:
+        line["clocks"] = ck
+    return _finish(line, rank, dist, ctx)
+
+
+WORKLOADS = {"chain16": run_chain16, "hubbard4x4": run_hubbard4x4, "ctpq26": run_ctpq26, "szz": run_szz}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,11 +635,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the extra FP64 measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["square4x8"] + sorted(WORKLOADS), default="square4x8",
+                    help="square4x8 (default): Lanczos steps on the 4x8 sector; the others measure the "
+                         "remaining workloads (one JSON line each)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("steps >= 1, warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "square4x8":
+        return WORKLOADS[args.workload](args)
     return run_native(args)
 
 

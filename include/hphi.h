@@ -293,6 +293,75 @@ HPHI_API int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
 HPHI_API int hphi_tpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv, double dtau,
                   int nmax, double *norm2_inout, double *e_host, double *h2_host, double *logd_host);
 
+/* ---- real-time evolution (Sec. 3.4) --------------------------------------------
+ * One step Phi(t + dt) = sum_{n<=nmax} (-i dt H)^n / n! Phi(t) for nvec complex
+ * columns of V (device, dtype C128 or C64, [D][nvec] complex, ld >= nvec),
+ * evaluated by Horner stages W <- Phi + (-i dt / j) H W, j = nmax .. 1.
+ * Out (host, per column, of the state before the step): norm2_host = <Phi|Phi>,
+ * e_host = <Phi|H|Phi> / <Phi|Phi>, h2_host = <H Phi|H Phi> / <Phi|Phi>; and
+ * norm2_new_host = <Phi(t + dt)|Phi(t + dt)> (the paper's accuracy check: it
+ * stays equal to the old norm up to the truncation of the series).
+ * V is overwritten with Phi(t + dt), not renormalised.  1 <= nmax <= 64,
+ * 1 <= nvec <= 64.  The library holds two workspace blocks of V's size.
+ * Errors: HPHI_E_INVAL, HPHI_E_NUMERIC (non-finite values), HPHI_E_CUDA. */
+HPHI_API int hphi_time_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv, double dt,
+                            int nmax, double *norm2_host, double *e_host, double *h2_host, double *norm2_new_host);
+
+/* ---- dynamical correlation functions (Sec. 3.2) ------------------------------
+ * D(z) = <Phi_ex| (z I - H)^{-1} |Phi_ex>, Phi_ex = O |Phi_0>; the spin
+ * structure factor is S^zz(q, w) = -Im D(w + i eta) for O = sum_l e^{i q l} S^z_l.
+ *
+ * hphi_apply_sz_sum: y = sum_l A_l S^z_l x with complex weights
+ * A_l = a_host[2l] + i a_host[2l+1] (l < n_sites; host array of 2 n_sites).
+ * S^z_l = n_l - 1/2 for the spin models (bit l of the spin string) and
+ * (n_{l up} - n_{l dn}) / 2 for Hubbard.  x: one real device vector (dtype
+ * F64 or F32, element stride ldx >= 1); y: two real device columns of the
+ * same dtype, y[r*ldy] = Re, y[r*ldy + 1] = Im (ldy >= 2; ldy = 2 is a complex
+ * vector).  x and y must not overlap (HPHI_E_INVAL).  Asynchronous. */
+HPHI_API int hphi_apply_sz_sum(hphi_ctx *ctx, const hphi_basis *basis, int dtype, const void *x, int64_t ldx, void *y,
+                               int64_t ldy, const double *a_host);
+
+/* hphi_shifted_krylov: D_c(z_j) = <b_c| (z_j I - H)^{-1} |b_c> for ncol real
+ * right-hand sides b_c (device, [D][ldb], dtype F64 or F32, 1 <= ncol <= 64)
+ * and nz complex shifts z_j = z_host[2j] + i z_host[2j+1], all from one
+ * Krylov run per column (the columns share every launch).
+ * Each column runs the Lanczos recurrence; the Galerkin solution of
+ * (z - H) x = b on the m-step Krylov space gives
+ *   D_c(z) = |b_c|^2 / (z - a_0 - b_1^2 / (z - a_1 - ... - b_{m-1}^2 / (z - a_{m-1})))
+ * and the residual |b_c - (z - H) x| / |b_c| = prod_{k=1..m} b_k / |u_k(z)|,
+ * u_1 = z - a_0, u_k = z - a_{k-1} - b_{k-1}^2 / u_{k-1}.  For real H and real
+ * b_c this iterate is the shifted COCG iterate of the paper's CG method and
+ * these residual norms are its convergence measure.  A complex excitation
+ * Phi = a + i b is passed as the two real columns a and b: (z - H)^{-1} is
+ * complex symmetric, so <Phi|G|Phi> = D_a + D_b.
+ * The run stops when every (column, shift) residual is <= opts->tol
+ * (checked every check_every steps), when every column has reached an
+ * invariant subspace (beta_{k+1} <= 64 eps max_j(|a_j| + b_j + b_{j+1})), or
+ * after max_steps.  Host outputs: g_host[2 (c nz + j) + {0, 1}] = Re, Im of
+ * D_c(z_j); resid_host[c nz + j] (nullable); alpha_host[c max_steps + k] and
+ * beta_host[c (max_steps + 1) + k] (nullable, zero past the column's steps;
+ * beta[0] = |b_c|).  A zero column gives D = 0 and residual 0.
+ * Returns HPHI_OK, HPHI_E_NOTCONV (tol > 0 not reached; outputs filled in),
+ * HPHI_E_NUMERIC (non-finite scalars) or an error.  The library holds three
+ * workspace blocks of D x ncol elements. */
+typedef struct hphi_krylov_opts {
+    int max_steps;
+    double tol;      /* relative residual of every shift; <= 0 runs max_steps */
+    int dtype;       /* HPHI_F64 or HPHI_F32 vectors (scalars are FP64) */
+    int check_every; /* host residual checks every this many steps (>= 1) */
+} hphi_krylov_opts;
+
+typedef struct hphi_krylov_result {
+    int steps;        /* Krylov steps taken */
+    int converged;    /* 1 if the tolerance (or invariant subspaces) ended the run */
+    double max_resid; /* largest relative residual over active columns and shifts */
+} hphi_krylov_result;
+
+HPHI_API int hphi_shifted_krylov(hphi_ctx *ctx, const hphi_ham *ham, const hphi_krylov_opts *opts, int ncol,
+                                 const void *b, int64_t ldb, int nz, const double *z_host, double *g_host,
+                                 double *resid_host, double *alpha_host, double *beta_host,
+                                 hphi_krylov_result *result);
+
 /* ---- host utility: symmetric tridiagonal eigenproblem ------------------------
  * All eigenvalues (ascending) of the n x n tridiagonal with diagonal a[0..n-1]
  * and off-diagonal b[1..n-1] (b[k] couples rows k-1 and k; b[0] unused), by the

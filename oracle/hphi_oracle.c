@@ -845,13 +845,15 @@ int orc_tpq_step(const orc_model *m, int nvec, int ncomp, double *V, double dtau
 /* Excitation operator of the dynamical structure factor (Sec. 3.2):         */
 /*   y = sum_l A_l S^z_l x,  A_l complex (A_l = e^{i q l} is the paper's      */
 /* O_spin at wave number q).  S^z_l = n_l - 1/2 for spin-1/2 (bit l of the    */
-/* spin string) and (n_{l up} - n_{l dn}) / 2 for Hubbard.  x is one real     */
-/* vector of length D; the result is y_re + i y_im.                           */
+/* spin string) and (n_{l up} - n_{l dn}) / 2 for Hubbard.  Rows [r0, r1)    */
+/* only: x[r - r0] is the input of row r and y_re + i y_im its output.        */
 /* ------------------------------------------------------------------------- */
 int orc_apply_sz_sum(const orc_model *m, const double *a_re, const double *a_im, const double *x, double *y_re,
-                     double *y_im)
+                     double *y_im, int64_t r0, int64_t r1)
 {
-    for (int64_t r = 0; r < m->D; r++) {
+    if (r0 < 0 || r1 > m->D || r0 > r1)
+        return ORC_EINVAL;
+    for (int64_t r = r0; r < r1; r++) {
         uint64_t su, sd;
         orc_row_state(m, r, &su, &sd);
         double f_re = 0.0, f_im = 0.0;
@@ -864,8 +866,63 @@ int orc_apply_sz_sum(const orc_model *m, const double *a_re, const double *a_im,
             f_re += a_re[l] * sz;
             f_im += a_im[l] * sz;
         }
-        y_re[r] = f_re * x[r];
-        y_im[r] = f_im * x[r];
+        y_re[r - r0] = f_re * x[r - r0];
+        y_im[r - r0] = f_im * x[r - r0];
     }
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Real-time evolution (Sec. 3.4): Phi(t + dt) = sum_{n<=nmax} (-i dt H)^n / n! Phi(t). */
+/* ------------------------------------------------------------------------- */
+
+/* One step for nvec complex columns of V (row-major [D][nvec] complex, stored
+ * re, im).  Term by term in complex arithmetic, H real:
+ *   T_0 = Phi,  T_n = (-i dt / n) H T_{n-1},  Phi' = sum_{n=0}^{nmax} T_n,
+ * where (-i c)(a + i b) = c b - i c a.  Outputs per column, for the state
+ * before the step: norm2[q] = <Phi|Phi>, e[q] = <Phi|H|Phi> / <Phi|Phi>, and
+ * norm2_new[q] = <Phi'|Phi'>.  V <- Phi' (not renormalised: the evolution is
+ * unitary up to the truncation of the series). */
+int orc_time_step(const orc_model *m, int nvec, double *V, double dt, int nmax, double *norm2, double *e,
+                  double *norm2_new)
+{
+    int64_t D = m->D, ld = 2 * (int64_t)nvec;
+    double *re = (double *)malloc(sizeof(double) * (size_t)D * 6);
+    if (!re)
+        return ORC_ENOMEM;
+    double *im = re + D, *hre = re + 2 * D, *him = re + 3 * D, *are = re + 4 * D, *aim = re + 5 * D;
+    int st = ORC_OK;
+    for (int q = 0; q < nvec && st == ORC_OK; q++) {
+        for (int64_t i = 0; i < D; i++) {
+            re[i] = V[i * ld + 2 * q];
+            im[i] = V[i * ld + 2 * q + 1];
+            are[i] = re[i];
+            aim[i] = im[i];
+        }
+        double nn = vdot(D, re, re) + vdot(D, im, im);
+        st = orc_apply(m, 1, re, 1, hre, 1, 1.0, 0.0, 0, D);
+        if (st == ORC_OK)
+            st = orc_apply(m, 1, im, 1, him, 1, 1.0, 0.0, 0, D);
+        norm2[q] = nn;
+        e[q] = (vdot(D, re, hre) + vdot(D, im, him)) / nn;
+        for (int n = 1; n <= nmax && st == ORC_OK; n++) {
+            st = orc_apply(m, 1, re, 1, hre, 1, 1.0, 0.0, 0, D);
+            if (st == ORC_OK)
+                st = orc_apply(m, 1, im, 1, him, 1, 1.0, 0.0, 0, D);
+            double c = dt / (double)n;
+            for (int64_t i = 0; i < D; i++) {
+                re[i] = c * him[i];
+                im[i] = -c * hre[i];
+                are[i] += re[i];
+                aim[i] += im[i];
+            }
+        }
+        norm2_new[q] = vdot(D, are, are) + vdot(D, aim, aim);
+        for (int64_t i = 0; i < D; i++) {
+            V[i * ld + 2 * q] = are[i];
+            V[i * ld + 2 * q + 1] = aim[i];
+        }
+    }
+    free(re);
+    return st;
 }

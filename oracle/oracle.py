@@ -75,7 +75,8 @@ def _L():
             "orc_lanczos": (i32, [vp, vp, i32, dbl, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), vp]),
             "orc_tpq_step": (i32, [vp, i32, i32, vp, dbl, i32, vp, vp, vp]),
-            "orc_apply_sz_sum": (i32, [vp, vp, vp, vp, vp, vp]),
+            "orc_apply_sz_sum": (i32, [vp, vp, vp, vp, vp, vp, i64, i64]),
+            "orc_time_step": (i32, [vp, i32, vp, dbl, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -228,18 +229,32 @@ class Model:
         k = steps.value
         return dict(status=st, steps=k, e0=e0.value, resid=res.value, alpha=alpha[:k], beta=beta[:k + 1], gs=gs)
 
-    def sz_sum(self, x: np.ndarray, A) -> np.ndarray:
-        """sum_l A_l S^z_l x for one real vector x and complex weights A[N]."""
+    def sz_sum(self, x: np.ndarray, A, rows: tuple[int, int] | None = None) -> np.ndarray:
+        """sum_l A_l S^z_l x for one real vector x and complex weights A[N];
+        with rows=(r0, r1), x and the result cover those rows only."""
+        r0, r1 = rows if rows is not None else (0, self.dim)
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
-        assert x.size == self.dim
+        assert x.size == r1 - r0
         A = np.asarray(A, dtype=np.complex128).reshape(-1)
         assert A.size == self.n_sites
         are, aim = np.ascontiguousarray(A.real), np.ascontiguousarray(A.imag)
-        yr, yi = np.zeros(self.dim), np.zeros(self.dim)
-        st = _L().orc_apply_sz_sum(self._h, _ptr(are), _ptr(aim), _ptr(x), _ptr(yr), _ptr(yi))
+        yr, yi = np.zeros(r1 - r0), np.zeros(r1 - r0)
+        st = _L().orc_apply_sz_sum(self._h, _ptr(are), _ptr(aim), _ptr(x), _ptr(yr), _ptr(yi), r0, r1)
         if st != 0:
             raise ValueError("sz_sum failed")
         return yr + 1j * yi
+
+    def time_step(self, V: np.ndarray, dt: float, nmax: int):
+        """One real-time step in place on complex V ([D] or [D][nvec]).
+        Returns (norm2, e) before the step and norm2 after it, per column."""
+        assert np.iscomplexobj(V) and V.dtype == np.complex128 and V.flags.c_contiguous
+        nvec = 1 if V.ndim == 1 else V.shape[1]
+        n2, e, n2n = np.zeros(nvec), np.zeros(nvec), np.zeros(nvec)
+        st = _L().orc_time_step(self._h, nvec, _ptr(V.view(np.float64)), float(dt), int(nmax), _ptr(n2), _ptr(e),
+                                _ptr(n2n))
+        if st != 0:
+            raise ValueError("time_step failed")
+        return n2, e, n2n
 
     def tpq_step(self, V: np.ndarray, dtau: float, nmax: int):
         """One cTPQ step in place on V ([D][nvec] real or complex). Returns e, h2, d."""

@@ -199,6 +199,7 @@ struct HvLaunch {
     const double *gamma_h;   // [ncol] host (nullptr: gamma_s)
     double alpha_s, gamma_s;
     const double *coef_dev;  // device [2*ncol]: alpha_c then gamma_c; overrides host values
+    int swap;                // 1: y[c] = alpha_c (H x)[c ^ 1] + ... (ncol even); complex rotation
     int red[3];              // reductions (Red codes)
     double *partials;        // per column slice: [grid][3][nc], slices back to back
     int nslice;              // column slices launched (filled by the launcher)

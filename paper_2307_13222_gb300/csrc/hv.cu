@@ -151,11 +151,26 @@ __global__ void __launch_bounds__(kThreads) k_hv(const HvArgs<T> a) {
             s.col0 = col0;
             s.act = act;
             visit_row<T>(a.P, hb, coef_sm, q, s);
+            // pair swap: the partner column is in this lane (CPL even) or in
+            // lane gl ^ 1 of the same row group, which runs the same rows
+            T hx[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; k++) hx[k] = s.acc[k];
+            if (a.swap) {
+                if constexpr (CPL % 2 == 0) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) hx[k] = s.acc[k ^ 1];
+                } else if constexpr (G >= 2) {
+                    const int lane = threadIdx.x & 31;
+                    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane - gl);
+                    hx[0] = __shfl_xor_sync(gmask, s.acc[0], 1);
+                }
+            }
             if (!act) continue;
             const int64_t row = s.row;
             T out[CPL];
 #pragma unroll
-            for (int k = 0; k < CPL; k++) out[k] = al[k] * s.acc[k];
+            for (int k = 0; k < CPL; k++) out[k] = al[k] * hx[k];
             if (use_beta) {
                 T yo[CPL];
                 load_cols_rw<T, CPL>(a.y + row * a.ldy + col0, yo);
@@ -269,6 +284,7 @@ int dispatch(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, bool pair_ok, boo
 
 template <typename T>
 int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
+    if (L.swap && (L.ncol % 2 != 0)) return set_err(ctx, HPHI_E_INVAL, "pair swap needs an even column count");
     const bool same_ld = L.ldx == L.ldy && (!L.v || L.ldv == L.ldx);
     int red_mode = -1;
     if (!L.red[0] && !L.red[1] && !L.red[2]) red_mode = 0;
@@ -344,6 +360,9 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         a.gamma_dev = L.coef_dev ? L.coef_dev + L.ncol + c0 : nullptr;
         for (int r = 0; r < 3; r++) a.red[r] = L.red[r];
         a.partials = L.partials ? L.partials + part_off : nullptr;
+        a.swap = L.swap;
+        if (L.swap && ((nc % 2) != 0 || (c0 % 2) != 0 || (fG == 1 && fcpl == 1) || (cpl == 1)))
+            return set_err(ctx, HPHI_E_INVAL, "pair swap: column slice [%d, %d) splits a pair", c0, c0 + nc);
         int grid = 0, st;
         if (fG) {
             set_traversal(ctx, ham, a.P, (double)nc * sizeof(T) < 4.0 ? 4.0 : (double)nc * sizeof(T));

@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(kThreads, (CPL == 1 && sizeof(T) == 4) ? 3 : 2
             T out[CPL];
 #pragma unroll
             for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k];
+            if constexpr (CPL % 2 == 0) {
+                if (a.swap) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k ^ 1];
+                }
+            }
             T *yr = a.y + roff;
             if (use_beta) {
                 T yo[CPL];
@@ -422,6 +428,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_hvc(const HvArgs<T> a) {
             T out[CPL];
 #pragma unroll
             for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k];
+            if constexpr (CPL % 2 == 0) {
+                if (a.swap) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k ^ 1];
+                }
+            }
             T *yr = a.y + roff;
             if (use_beta) {
                 T yo[CPL];

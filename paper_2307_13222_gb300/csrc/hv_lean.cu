@@ -266,6 +266,12 @@ __global__ void __launch_bounds__(kThreads, (CPL >= 4 || sizeof(T) == 8) ? 2 : 3
             T out[CPL];
 #pragma unroll
             for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k];
+            if constexpr (CPL % 2 == 0) {
+                if (a.swap) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) out[k] = al[k] * acc[k ^ 1];
+                }
+            }
             T *yr = a.y + roff;
             if (use_beta) {
                 T yo[CPL];

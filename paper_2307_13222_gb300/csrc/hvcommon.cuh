@@ -52,6 +52,7 @@ struct HvArgs {
     const double *gamma_dev;
     int red[3];
     double *partials;  // [grid][3][ncol]
+    int swap;          // out[c] takes (H x)[c ^ 1]: multiplication by -i / +i of complex columns
 };
 
 inline HvTables make_tables(const hphi_ham *ham, int real_dtype) {

@@ -44,6 +44,14 @@ class _LanczosResult(C.Structure):
                 ("breakdown", C.c_int)]
 
 
+class _KrylovOpts(C.Structure):
+    _fields_ = [("max_steps", C.c_int), ("tol", C.c_double), ("dtype", C.c_int), ("check_every", C.c_int)]
+
+
+class _KrylovResult(C.Structure):
+    _fields_ = [("steps", C.c_int), ("converged", C.c_int), ("max_resid", C.c_double)]
+
+
 _lib = None
 vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
 _SIGS = {
@@ -77,6 +85,10 @@ _SIGS = {
     "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
     "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
     "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
+    "hphi_apply_sz_sum": (i32, [vp, vp, i32, vp, i64, vp, i64, vp]),
+    "hphi_time_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_shifted_krylov": (i32, [vp, vp, C.POINTER(_KrylovOpts), i32, vp, i64, i32, vp, vp, vp, vp, vp,
+                                  C.POINTER(_KrylovResult)]),
 }
 
 
@@ -368,6 +380,107 @@ def hphi_tpq_step(ham: Hamiltonian, V, dtau: float, nmax: int, norm2: np.ndarray
     ctx.check(ctx.lib.hphi_tpq_step(ctx.h, ham.h, _dtype_code(V), nv, pv, ld, float(dtau), int(nmax), _np(norm2),
                                     _np(e), _np(h2), _np(logd)))
     return e, h2, logd
+
+
+def hphi_time_step(ham: Hamiltonian, V, dt: float, nmax: int):
+    """One real-time step in place on complex V ([D] or [D][nvec], C128/C64).
+    Returns (norm2, e, h2) of the state before the step and norm2 after it."""
+    ctx = ham.ctx
+    pv, nv, ld = _vec(V)
+    dc = _dtype_code(V)
+    if dc not in (C128, C64):
+        raise ValueError("real-time evolution needs complex vectors")
+    n2, e, h2, n2n = np.zeros(nv), np.zeros(nv), np.zeros(nv), np.zeros(nv)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_time_step(ctx.h, ham.h, dc, nv, pv, ld, float(dt), int(nmax), _np(n2), _np(e), _np(h2),
+                                     _np(n2n)))
+    return n2, e, h2, n2n
+
+
+def hphi_apply_sz_sum(basis: Basis, x, y, A):
+    """y = sum_l A_l S^z_l x (Sec. 3.2 excitation operator).  x: real CUDA
+    vector [D] (any element stride); y: complex CUDA vector [D] or real
+    [D][>=2] (Re in column 0, Im in column 1) of x's precision; A: N complex
+    weights (e^{i q l} for S^z(q))."""
+    import torch
+    ctx = basis.ctx
+    if not (x.is_cuda and y.is_cuda):
+        raise ValueError("libhphi takes CUDA tensors only (no CPU path)")
+    if x.dim() != 1 or x.dtype not in (torch.float64, torch.float32):
+        raise ValueError("x must be a real [D] vector")
+    if y.is_complex():
+        if y.dim() != 1 or y.stride(0) != 1:
+            raise ValueError("complex y must be a contiguous [D] vector")
+        yr = torch.view_as_real(y)
+        ldy = 2
+    else:
+        if y.dim() != 2 or y.stride(1) != 1 or y.shape[1] < 2:
+            raise ValueError("real y must be [D][>=2] with unit column stride")
+        yr, ldy = y, y.stride(0)
+    if yr.dtype != x.dtype:
+        raise ValueError("x and y must have the same precision")
+    a = np.asarray(A, dtype=np.complex128).reshape(-1)
+    if a.size != basis.n_sites:
+        raise ValueError(f"need {basis.n_sites} weights")
+    ah = np.ascontiguousarray(np.stack([a.real, a.imag], axis=1).reshape(-1))
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_apply_sz_sum(ctx.h, basis.h, _dtype_code(x), C.c_void_p(x.data_ptr()), x.stride(0),
+                                        C.c_void_p(yr.data_ptr()), ldy, _np(ah)))
+    return y
+
+
+def hphi_shifted_krylov(ham: Hamiltonian, B, z, max_steps: int, tol: float, check_every: int = 1):
+    """D_c(z_j) = <b_c|(z_j - H)^{-1}|b_c> for the real CUDA columns of B ([D]
+    or [D][ncol], F64 or F32) and complex shifts z.  Returns a dict with G
+    [ncol][nz] complex, resid [ncol][nz], steps, converged, status, max_resid,
+    alpha / beta per column (beta[0] = |b_c|).  NOTCONV is reported, not raised."""
+    ctx = ham.ctx
+    pv, nc, ld = _vec(B)
+    dc = _dtype_code(B)
+    if dc not in (F64, F32):
+        raise ValueError("right-hand sides must be real (split a complex vector into its two parts)")
+    zz = np.asarray(z, dtype=np.complex128).reshape(-1)
+    zh = np.ascontiguousarray(np.stack([zz.real, zz.imag], axis=1).reshape(-1))
+    nz = zz.size
+    g = np.zeros(2 * nc * nz)
+    resid = np.zeros(nc * nz)
+    alpha = np.zeros(nc * max_steps)
+    beta = np.zeros(nc * (max_steps + 1))
+    opts = _KrylovOpts(max_steps, tol, dc, check_every)
+    res = _KrylovResult()
+    ctx._sync_stream()
+    st = ctx.lib.hphi_shifted_krylov(ctx.h, ham.h, C.byref(opts), nc, pv, ld, nz, _np(zh), _np(g), _np(resid),
+                                     _np(alpha), _np(beta), C.byref(res))
+    if st not in (HPHI_OK, -4):
+        ctx.check(st)
+    G = (g[0::2] + 1j * g[1::2]).reshape(nc, nz)
+    return dict(G=G, resid=resid.reshape(nc, nz), steps=res.steps, converged=bool(res.converged), status=st,
+                max_resid=res.max_resid, alpha=alpha.reshape(nc, max_steps), beta=beta.reshape(nc, max_steps + 1))
+
+
+def hphi_szz_spectrum(ham: Hamiltonian, basis: Basis, gs, qs, z, max_steps: int, tol: float,
+                      check_every: int = 4):
+    """S^zz(q, z) = -Im <Phi_q|(z - H)^{-1}|Phi_q>, Phi_q = sum_l e^{i q l} S^z_l gs,
+    for every wave number in qs at once: the excitations fill the real block
+    [D][2 nq] (Re, Im of each q) and one shifted-Krylov run covers all columns.
+    Returns (S [nq][nz], D [nq][nz] complex, the shifted-Krylov dict)."""
+    import torch
+    qs = np.atleast_1d(np.asarray(qs, dtype=np.float64))
+    nq = qs.size
+    L = basis.n_sites
+    ph = [np.exp(1j * q * np.arange(L)) for q in qs]
+    # the imaginary part of e^{i q l} vanishes for q = 0 and q = pi (up to
+    # rounding of sin): those wave numbers need one real column
+    two = [bool(np.abs(p.imag).max() > 1e-12) for p in ph]
+    col = np.concatenate([[0], np.cumsum([2 if t else 1 for t in two])])
+    blk = torch.empty((basis.dim, 2 * nq), dtype=gs.dtype, device=gs.device)
+    for k in range(nq):
+        hphi_apply_sz_sum(basis, gs, blk[:, 2 * k:2 * k + 2], ph[k] if two[k] else ph[k].real)
+    keep = [2 * k + j for k in range(nq) for j in range(2 if two[k] else 1)]
+    rhs = blk[:, keep].contiguous()
+    r = hphi_shifted_krylov(ham, rhs, z, max_steps, tol, check_every)
+    Dq = np.stack([r["G"][col[k]] + (r["G"][col[k] + 1] if two[k] else 0.0) for k in range(nq)])
+    return -Dq.imag, Dq, r
 
 
 def hphi_dump_pattern(ham: Hamiltonian, row0: int, row1: int):

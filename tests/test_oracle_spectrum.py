@@ -170,3 +170,13 @@ def test_cocg_iterate_equals_lanczos_galerkin_iterate():
         assert it == k
         assert np.abs(G2 - G).max() < 1e-11 * np.abs(G).max()
         assert np.allclose(res2, res, rtol=1e-10, atol=0)
+
+
+def test_sz_sum_row_range_is_a_slice_of_the_full_result():
+    m = O.Model("HUBBARD", 6, 3, 2, hubbard_terms(6, chain(6), t=1.0, U=2.0))
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=6) + 1j * rng.normal(size=6)
+    x = rng.normal(size=m.dim)
+    full = m.sz_sum(x, A)
+    for r0, r1 in ((0, 7), (13, 200), (m.dim - 5, m.dim), (40, 40)):
+        assert np.array_equal(m.sz_sum(x[r0:r1], A, rows=(r0, r1)), full[r0:r1])
