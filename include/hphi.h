@@ -162,11 +162,17 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *   HPHI_TUNE_VARIANT     -1 = automatic (default); spin models: 1 = neighbour
  *                         ranks computed on the fly from Lin's ja table, 0 =
  *                         precomputed neighbour lists (also enables the
- *                         one-thread-per-row kernel for Hubbard)
+ *                         one-thread-per-row kernel for Hubbard), 2 = staged:
+ *                         the row block's x in shared memory and low-half
+ *                         ranks from shared tables (S^z sector, one column,
+ *                         N_lo <= 16; automatic there for FP32 data)
  *   HPHI_TUNE_COOP        32-column rows: 1 = the lanes of a row split the
  *                         bond evaluation and share targets, 0 = every lane
  *                         evaluates every bond, -1 = 1 for FP32 and 0 for
  *                         FP64 data (default)
+ *   HPHI_TUNE_STAGED_LISTS staged kernel: 1 = low-low targets and flipped
+ *                         ranks from the per-low-half lists, 0 = from the
+ *                         shared rank tables (default)
  * Results do not depend on the knobs except through summation order of the
  * reductions (still deterministic for fixed knobs).  HPHI_E_INVAL for an
  * unknown knob or value. */
@@ -175,6 +181,7 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
 #define HPHI_TUNE_L2_HINTS 2
 #define HPHI_TUNE_VARIANT 3
 #define HPHI_TUNE_COOP 4
+#define HPHI_TUNE_STAGED_LISTS 5
 HPHI_API int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value);
 HPHI_API int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value);
 

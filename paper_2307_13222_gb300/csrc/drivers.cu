@@ -82,6 +82,82 @@ int tridiag_ql(int n, double *d, double *e, double *z) {
     return HPHI_OK;
 }
 
+// Solves (T - s I) x = r in place (r -> x) for the symmetric tridiagonal T with
+// diagonal a[0..n-1] and off-diagonal b[1..n-1], by Gaussian elimination with
+// partial pivoting (U keeps two super-diagonals); a zero pivot becomes `tiny`.
+static void tridiag_shift_solve(int n, const double *a, const double *b, double s, double tiny, double *r) {
+    std::vector<double> u0(n), u1(n), u2(n), rhs(n);
+    double cd = a[0] - s, ce = n > 1 ? b[1] : 0.0, cf = 0.0, cr = r[0];
+    for (int i = 0; i < n; i++) {
+        if (i == n - 1) {
+            u0[i] = cd != 0.0 ? cd : tiny;
+            u1[i] = u2[i] = 0.0;
+            rhs[i] = cr;
+            break;
+        }
+        const double g = b[i + 1], hd = a[i + 1] - s, hk = i + 2 < n ? b[i + 2] : 0.0, hr = r[i + 1];
+        if (fabs(cd) >= fabs(g)) {  // pivot on the current row
+            if (cd == 0.0) cd = tiny;
+            const double m = g / cd;
+            u0[i] = cd;
+            u1[i] = ce;
+            u2[i] = cf;
+            rhs[i] = cr;
+            cd = hd - m * ce;
+            ce = hk - m * cf;
+            cr = hr - m * cr;
+        } else {  // pivot on the next row
+            const double m = cd / g;
+            u0[i] = g;
+            u1[i] = hd;
+            u2[i] = hk;
+            rhs[i] = hr;
+            cd = ce - m * hd;
+            ce = cf - m * hk;
+            cr = cr - m * hr;
+        }
+        cf = 0.0;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double v = rhs[i];
+        if (i + 1 < n) v -= u1[i] * r[i + 1];
+        if (i + 2 < n) v -= u2[i] * r[i + 2];
+        r[i] = v / u0[i];
+    }
+}
+
+// Lowest eigenvalue of T_m (QL without eigenvectors, O(m^2)) and the last
+// component of its normalised eigenvector (inverse iteration, O(m)): what a
+// convergence check needs.  The full eigenvector is formed only at the end.
+static int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, double *ylast) {
+    std::vector<double> d(alpha, alpha + m), e(m, 0.0), b(m + 1, 0.0);
+    for (int j = 1; j < m; j++) {
+        b[j] = sqrt(beta2[j]);
+        e[j - 1] = b[j];
+    }
+    int st = tridiag_ql(m, d.data(), e.data(), nullptr);
+    if (st) return st;
+    double t = d[0], scale = 0.0;
+    for (int j = 0; j < m; j++) {
+        t = d[j] < t ? d[j] : t;
+        scale = fabs(d[j]) > scale ? fabs(d[j]) : scale;
+    }
+    for (int j = 1; j < m; j++) scale = b[j] > scale ? b[j] : scale;
+    std::vector<double> y(m, 1.0 / sqrt((double)m));
+    const double tiny = DBL_EPSILON * (scale > 0.0 ? scale : 1.0);
+    for (int it = 0; it < 3; it++) {
+        tridiag_shift_solve(m, alpha, b.data(), t, tiny, y.data());
+        double nn = 0.0;
+        for (int j = 0; j < m; j++) nn += y[j] * y[j];
+        nn = sqrt(nn);
+        if (!(nn > 0.0) || !isfinite(nn)) return HPHI_E_NUMERIC;
+        for (int j = 0; j < m; j++) y[j] /= nn;
+    }
+    *theta = t;
+    *ylast = fabs(y[m - 1]);
+    return HPHI_OK;
+}
+
 namespace {
 
 enum LzMode { LZ_INIT = 0, LZ_PREP_A = 1, LZ_ALPHA = 2, LZ_BETA = 3 };
@@ -282,15 +358,10 @@ static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
             }
             if (flag > 0 && !(brk && mstop <= flag - 1))
                 return fail(set_err(ctx, HPHI_E_NUMERIC, "Lanczos: non-finite scalars at step %d", flag - 1));
-            std::vector<double> a(alpha_h.begin(), alpha_h.begin() + mstop), b(mstop, 0.0), ev(mstop),
-                Z((size_t)mstop * mstop);
-            for (int j = 1; j < mstop; j++) b[j] = sqrt(beta2_h[j]);
-            if ((st = hphi_tridiag_eigen(mstop, a.data(), b.data(), ev.data(), Z.data())))
+            double yl = 0.0;
+            if ((st = lowest_ritz(mstop, alpha_h.data(), beta2_h.data(), &theta, &yl)))
                 return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
-            theta = ev[0];
-            y.assign(mstop, 0.0);
-            for (int i = 0; i < mstop; i++) y[i] = Z[(size_t)i * mstop];
-            resid_est = sqrt(beta2_h[mstop]) * fabs(y[mstop - 1]);
+            resid_est = sqrt(beta2_h[mstop]) * yl;
             steps = mstop;
             if (brk) break;
             if (opts->tol > 0.0 && mstop >= 2 && resid_est <= opts->tol * (fabs(theta) > 1.0 ? fabs(theta) : 1.0)) {
@@ -310,6 +381,14 @@ static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
     if (beta_host)
         for (int j = 0; j <= M; j++) beta_host[j] = (j >= 1 && j <= m) ? sqrt(beta2_h[j]) : 0.0;
     if (gs_out) {
+        {
+            std::vector<double> a(alpha_h.begin(), alpha_h.begin() + m), b(m, 0.0), ev(m), Z((size_t)m * m);
+            for (int j = 1; j < m; j++) b[j] = sqrt(beta2_h[j]);
+            if ((st = hphi_tridiag_eigen(m, a.data(), b.data(), ev.data(), Z.data())))
+                return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
+            y.assign(m, 0.0);
+            for (int i = 0; i < m; i++) y[i] = Z[(size_t)i * m];
+        }
         // x = sum_j y_j v_j, as gs -= sum_j (-y_j) v_j from zero
         std::vector<double> ny(m);
         for (int j = 0; j < m; j++) ny[j] = -y[j];
@@ -384,8 +463,16 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
     if ((st = launch_dot(ctx, dt, 0, D, 1, cur, 1, cur, 1, red))) return fail(st);
     k_lz<<<1, 32, 0, ctx->stream>>>(LZ_INIT, 0, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
 
-    // eigen-solution of T_m from the host copies
+    // convergence check: lowest Ritz value and the residual estimate
     auto solve_T = [&](int m) -> int {
+        double yl = 0.0;
+        int s2 = lowest_ritz(m, alpha_h.data(), beta2_h.data(), &theta, &yl);
+        if (s2) return s2;
+        resid_est = sqrt(beta2_h[m]) * yl;
+        return HPHI_OK;
+    };
+    // the Ritz vector of T_m (for the ground-state pass)
+    auto full_y = [&](int m) -> int {
         std::vector<double> a(alpha_h.begin(), alpha_h.begin() + m), b(m, 0.0), ev(m), Z((size_t)m * m);
         for (int j = 1; j < m; j++) b[j] = sqrt(beta2_h[j]);
         int s2 = hphi_tridiag_eigen(m, a.data(), b.data(), ev.data(), Z.data());
@@ -393,7 +480,6 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
         theta = ev[0];
         y.assign(m, 0.0);
         for (int i = 0; i < m; i++) y[i] = Z[(size_t)i * m];
-        resid_est = sqrt(beta2_h[m]) * fabs(y[m - 1]);
         return HPHI_OK;
     };
 
@@ -482,6 +568,7 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
         for (int j = 0; j <= M; j++) beta_host[j] = (j >= 1 && j <= m) ? sqrt(beta2_h[j]) : 0.0;
 
     if (gs_out) {
+        if ((st = full_y(m))) return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
         // second pass: regenerate w_k with the stored alpha/beta (the same
         // kernels on the same inputs reproduce the first pass bit for bit) and
         // accumulate x = sum_k y_k v_k = sum_k (y_k / beta_k) w_k

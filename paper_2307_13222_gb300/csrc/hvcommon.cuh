@@ -139,5 +139,8 @@ int launch_lean(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int cpl,
 // On-the-fly-rank kernel (hv_fly.cu), spin models: G lanes per row, CPL columns per lane.
 template <typename T>
 int launch_fly(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int G, int cpl, int red_mode, int *grid);
+// staged kernel (hv_staged.cu): spin sector, one column, N_lo <= 16
+template <typename T>
+int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
 
 }  // namespace hphi

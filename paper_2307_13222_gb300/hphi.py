@@ -243,10 +243,10 @@ class Hamiltonian:
         self.h = h
         self.dim = int(ctx.lib.hphi_ham_dim(h))
 
-    TUNE = {"inner_bits": 0, "split": 1, "l2_hints": 2, "variant": 3, "coop": 4}
+    TUNE = {"inner_bits": 0, "split": 1, "l2_hints": 2, "variant": 3, "coop": 4, "staged_lists": 5}
 
     def set_tuning(self, **knobs):
-        """Launch knobs of the H*x kernel: inner_bits, split, l2_hints, variant, coop."""
+        """Launch knobs of the H*x kernel: inner_bits, split, l2_hints, variant, coop, staged_lists."""
         for k, v in knobs.items():
             self.ctx.check(self.ctx.lib.hphi_ham_set_tuning(self.h, self.TUNE[k], int(v)))
 

@@ -179,7 +179,8 @@ def test_rrg26_block32_full_size_sampled(dtype):
 
 
 @pytest.mark.parametrize("variant,split,hints,inner", [(-1, 1, 1, -1), (0, 1, 1, -1), (1, 1, 1, -1),
-                                                       (0, 3, 0, 2), (1, 2, 0, 1), (1, 4, 1, 0), (-1, 8, 1, 32)])
+                                                       (0, 3, 0, 2), (1, 2, 0, 1), (1, 4, 1, 0), (-1, 8, 1, 32),
+                                                       (2, 1, 1, -1), (2, 1, 0, 3)])
 @pytest.mark.parametrize("shape", ["sector", "full", "hubbard"])
 @pytest.mark.parametrize("nvec", [1, 2, 32])
 def test_kernel_variants_and_knobs(variant, split, hints, inner, shape, nvec):
@@ -214,3 +215,29 @@ def test_wide_rows_cooperative_knob(coop, split, shape):
     for dtype in (torch.float64, torch.float32):
         _check(m, h, dtype, 32, alpha=1.1, beta=0.0, seed=20 + split)
         _check(m, h, dtype, 32, alpha=-0.6, beta=0.25, seed=21 + split)
+
+
+@pytest.mark.parametrize("N,nup", [(12, 6), (13, 4), (17, 8), (20, 7), (22, 11)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lists", [0, 1])
+def test_staged_kernel(N, nup, dtype, lists):
+    """Shared-memory staged kernel (spin sector, one column): low halves of
+    4 to 11 bits, every popcount class, random XXZ couplings incl. zero Jxy."""
+    rng = random.Random(N * 31 + nup)
+    pairs = rng.sample(list(itertools.combinations(range(N), 2)), 3 * N)
+    terms = [("XXZ", i, j, 0, rng.uniform(-1, 2), rng.uniform(-1, 2) if k % 7 else 0.0)
+             for k, (i, j) in enumerate(pairs)]
+    m, b, h = pair("SPIN_HALF", N, nup, 0, terms)
+    h.set_tuning(variant=2, staged_lists=lists)
+    _check(m, h, dtype, 1, alpha=0.8, beta=0.0, seed=N)
+    _check(m, h, dtype, 1, alpha=-1.1, beta=0.35, seed=N + 1)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lists", [0, 1])
+def test_staged_square_4x8_full_size_sampled(dtype, lists):
+    m, b, h = pair("SPIN_HALF", 32, 16, 0, heisenberg_terms(square(8, 4), 1.0))
+    h.set_tuning(variant=2, staged_lists=lists)
+    rng = np.random.default_rng(18)
+    rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
+    assert _sampled_rows(m, h, dtype, 1, rows, 52) < (1e-15 if dtype == torch.float64 else 1e-6)

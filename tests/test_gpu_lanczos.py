@@ -117,3 +117,18 @@ def test_reorth_storage_beyond_device_memory_is_nomem():
     with pytest.raises(hphi.HphiError) as ei:
         hphi.hphi_lanczos(h, v0, steps, 1e-10, reorth=True)
     assert ei.value.code == -2
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_chain16_each_single_column_kernel(variant):
+    """The fused Lanczos step (reductions <x,y> and |y|^2 of the ground-state
+    pass) through the table-driven and the staged kernels."""
+    cfg = configs.heisenberg_chain16()
+    m, b, h = pair(cfg["model"], cfg["n_sites"], cfg["n_up"], 0, cfg["terms"])
+    h.set_tuning(variant=variant)
+    v0 = random_vectors(m.dim, 1, cfg["seed"])[:, 0]
+    ro = m.lanczos(v0, cfg["max_steps"], cfg["tol"], want_gs=True)
+    gs = torch.empty(m.dim, dtype=torch.float64, device="cuda")
+    r = hphi.hphi_lanczos(h, torch.from_numpy(v0).cuda(), cfg["max_steps"], cfg["tol"], gs_out=gs)
+    assert r["converged"] and abs(r["e0"] - ro["e0"]) <= 1e-10 * abs(ro["e0"])
+    assert abs(np.dot(gs.cpu().numpy(), ro["gs"])) >= 1 - 1e-10 and r["resid"] < 1e-9
