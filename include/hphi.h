@@ -285,6 +285,85 @@ typedef struct hphi_lanczos_result {
 HPHI_API int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0, void *gs_out,
                  double *alpha_host, double *beta_host, hphi_lanczos_result *result);
 
+/* ---- many small problems at once: the Lanczos driver in batched form -------------
+ * hphi_lanczos_batch: the ground state of nprob independent problems (as
+ * hphi_lanczos computes it: same recurrence, same stopping rule evaluated
+ * after every step, two-pass ground-state vector; FP64, no
+ * reorthogonalisation), one thread block per problem.  hams[p] (may repeat),
+ * v0[p]: device FP64 start vector of length D_p; gs_out: null, or per
+ * problem a device FP64 vector of length D_p or null.  opts->check_every is
+ * the number of steps one launch runs (the stopping step does not depend on
+ * it; larger values mean fewer launches and host checks).  Per problem:
+ * results[p] (e0, resid_est, resid = |H gs - e0 gs| when gs_out[p] is given
+ * else -1, steps, breakdown) and status[p] = HPHI_OK, HPHI_E_NOTCONV (tol > 0
+ * not reached in max_steps), HPHI_E_NUMERIC or HPHI_E_INVAL (zero start
+ * vector).  Returns HPHI_OK when every status is OK, otherwise an error code
+ * from the statuses (errors before HPHI_E_NOTCONV).  A problem's results do
+ * not depend on the rest of the batch (bit for bit).  Limits: D_p <= 2^26,
+ * at most 256 merged terms, S^z sectors of at most 32 sites, nprob <= 65535.
+ * Workspace: 3 D_p + 2 max_steps + 3 doubles per problem. */
+HPHI_API int hphi_lanczos_batch(hphi_ctx *ctx, int nprob, hphi_ham *const *hams, const void *const *v0,
+                                void *const *gs_out, const hphi_lanczos_opts *opts, hphi_lanczos_result *results,
+                                int *status);
+
+/* ---- serving loop: continuous batching of ground-state and spectrum requests -----
+ * A server owns a device arena of opts->mem_budget bytes for the workspaces of
+ * small problems (D <= small_max_dim, at most 256 merged terms), which run on
+ * the batched block engine of hphi_lanczos_batch: every running recurrence is
+ * one thread block, and hphi_server_step launches the next opts->chunk steps
+ * of all of them at once, then evaluates each stopping rule after every step,
+ * retires finished requests (freeing their memory at once) and admits queued
+ * ones (FIFO) whose workspace fits and for which block slots are free.
+ * Larger problems go to a second lane: a worker thread that runs the
+ * grid-wide drivers on its own CUDA stream, concurrently.  A request's result
+ * does not depend on the other requests (bit for bit).
+ * Requests: HPHI_REQ_GROUND, the ground-state energy (hphi_lanczos' recurrence
+ * and stopping rule, FP64, Philox start vector of `seed`, residual `tol`);
+ * HPHI_REQ_SPECTRUM, in addition D(z_j) = <Phi|(z_j - H)^{-1}|Phi> for
+ * Phi = sum_l e^{i q l} S^z_l Phi_0 and z_j = E0 + omega[j] + i eta (Sec. 3.2),
+ * by the shifted-Krylov recurrences of Phi's real and imaginary parts, stopped
+ * when every shift's relative residual is <= tol.  The Hamiltonian is the
+ * caller's and must outlive the request; `omega` is copied at submission.
+ * hphi_server_result: done = 1 once finished; the times are seconds on the
+ * server's clock (hphi_server_clock); d_out (nullable, 2 nz doubles) receives
+ * D(z_j) as re, im pairs.  Errors: HPHI_E_INVAL (bad options / request /
+ * unknown id), HPHI_E_NOMEM, HPHI_E_CUDA; a request's own failure is in its
+ * reply's status. */
+typedef struct hphi_server hphi_server;
+typedef struct hphi_server_opts {
+    double mem_budget;     /* bytes of the device arena */
+    int max_active;        /* recurrences (thread blocks) at once; 0: 2 x SMs */
+    int chunk;             /* Lanczos steps per server step; 0: 16 */
+    int64_t small_max_dim; /* larger problems use the grid lane; 0: 2^20 */
+} hphi_server_opts;
+
+#define HPHI_REQ_GROUND 0
+#define HPHI_REQ_SPECTRUM 1
+
+typedef struct hphi_request {
+    int kind;
+    hphi_ham *ham;
+    uint64_t seed;
+    int max_steps;
+    double tol;
+    double q, eta;        /* spectrum: wave number, broadening */
+    int nz;               /* spectrum: number of shifts */
+    const double *omega;  /* spectrum: [nz] frequencies above E0 */
+} hphi_request;
+
+typedef struct hphi_reply {
+    int done, status, steps, krylov_steps, lane;
+    double e0, max_resid;
+    double t_submit, t_start, t_done;
+} hphi_reply;
+
+HPHI_API int hphi_server_create(hphi_ctx *ctx, const hphi_server_opts *opts, hphi_server **out);
+HPHI_API void hphi_server_destroy(hphi_server *server);
+HPHI_API double hphi_server_clock(const hphi_server *server);
+HPHI_API int hphi_server_submit(hphi_server *server, const hphi_request *request, int64_t *id);
+HPHI_API int hphi_server_step(hphi_server *server, int *n_running, int *n_queued);
+HPHI_API int hphi_server_result(hphi_server *server, int64_t id, hphi_reply *reply, double *d_out);
+
 /* ---- canonical TPQ step (Sec. 3.5.1) -----------------------------------------
  * One step Phi_{k+1} = U_c(dtau) Phi_k, U_c = sum_{n<=nmax} (-dtau H/2)^n / n!,
  * for nvec independent columns of V (device, dtype F64/F32/C128/C64, [D][nvec],

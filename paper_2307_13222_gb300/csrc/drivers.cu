@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "hphi_internal.cuh"
@@ -126,36 +127,100 @@ static void tridiag_shift_solve(int n, const double *a, const double *b, double 
     }
 }
 
-// Lowest eigenvalue of T_m (QL without eigenvectors, O(m^2)) and the last
-// component of its normalised eigenvector (inverse iteration, O(m)): what a
-// convergence check needs.  The full eigenvector is formed only at the end.
-static int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, double *ylast) {
-    std::vector<double> d(alpha, alpha + m), e(m, 0.0), b(m + 1, 0.0);
-    for (int j = 1; j < m; j++) {
-        b[j] = sqrt(beta2[j]);
-        e[j - 1] = b[j];
+// Number of eigenvalues of T (diagonal a, off-diagonal b[1..n-1]) below x, from
+// the signs of the LDL^T pivots (Sturm sequence); a zero pivot becomes -tiny.
+static int sturm_below(int n, const double *a, const double *b, double x, double tiny) {
+    int c = 0;
+    double d = a[0] - x;
+    if (d == 0.0) d = -tiny;
+    c += d < 0.0;
+    for (int i = 1; i < n; i++) {
+        d = a[i] - x - b[i] * b[i] / d;
+        if (d == 0.0) d = -tiny;
+        c += d < 0.0;
     }
-    int st = tridiag_ql(m, d.data(), e.data(), nullptr);
-    if (st) return st;
-    double t = d[0], scale = 0.0;
+    return c;
+}
+
+// Lowest eigenvalue of T_m and the last component of its normalised
+// eigenvector: what a convergence check needs, at O(m) cost.  With a warm
+// start (*warm finite: e.g. the lowest Ritz value of an earlier T_j, an upper
+// bound of this one) Rayleigh-quotient iteration converges in a few O(m)
+// solves; its answer is accepted only if the Sturm count shows it is the
+// lowest eigenvalue, otherwise (or without a warm start) bisection on the
+// Sturm count decides.  *warm receives the result.  The full eigenvector is
+// formed only at the end of a run.
+int lowest_ritz_warm(int m, const double *alpha, const double *beta2, double *warm, double *theta, double *ylast) {
+    std::vector<double> b(m + 1, 0.0), y(m);
+    double lo = alpha[0], scale = 0.0;
+    for (int j = 1; j < m; j++) b[j] = sqrt(beta2[j]);
     for (int j = 0; j < m; j++) {
-        t = d[j] < t ? d[j] : t;
-        scale = fabs(d[j]) > scale ? fabs(d[j]) : scale;
+        const double r = (j > 0 ? b[j] : 0.0) + (j + 1 < m ? b[j + 1] : 0.0);
+        lo = alpha[j] - r < lo ? alpha[j] - r : lo;  // Gershgorin lower bound
+        scale = fabs(alpha[j]) + r > scale ? fabs(alpha[j]) + r : scale;
     }
-    for (int j = 1; j < m; j++) scale = b[j] > scale ? b[j] : scale;
-    std::vector<double> y(m, 1.0 / sqrt((double)m));
-    const double tiny = DBL_EPSILON * (scale > 0.0 ? scale : 1.0);
-    for (int it = 0; it < 3; it++) {
-        tridiag_shift_solve(m, alpha, b.data(), t, tiny, y.data());
+    if (!isfinite(scale)) return HPHI_E_NUMERIC;
+    if (scale == 0.0) scale = 1.0;
+    const double tiny = DBL_MIN * 4.0, pivot_floor = DBL_EPSILON * scale;
+    auto normalise = [&]() -> bool {
         double nn = 0.0;
         for (int j = 0; j < m; j++) nn += y[j] * y[j];
         nn = sqrt(nn);
-        if (!(nn > 0.0) || !isfinite(nn)) return HPHI_E_NUMERIC;
+        if (!(nn > 0.0) || !isfinite(nn)) return false;
         for (int j = 0; j < m; j++) y[j] /= nn;
+        return true;
+    };
+    auto rayleigh = [&]() {
+        double s = 0.0;
+        for (int j = 0; j < m; j++) {
+            double ty = alpha[j] * y[j];
+            if (j > 0) ty += b[j] * y[j - 1];
+            if (j + 1 < m) ty += b[j + 1] * y[j + 1];
+            s += y[j] * ty;
+        }
+        return s;
+    };
+    double t = 0.0;
+    bool ok = false;
+    if (warm && isfinite(*warm) && m > 1) {
+        double sig = *warm;
+        for (int j = 0; j < m; j++) y[j] = 1.0 / sqrt((double)m);
+        for (int it = 0; it < 8; it++) {
+            tridiag_shift_solve(m, alpha, b.data(), sig, pivot_floor, y.data());
+            if (!normalise()) break;
+            const double s2 = rayleigh();
+            const bool done = fabs(s2 - sig) <= 4.0 * DBL_EPSILON * scale;
+            sig = s2;
+            if (done) {
+                ok = sturm_below(m, alpha, b.data(), sig + 16.0 * DBL_EPSILON * scale, tiny) == 1;
+                break;
+            }
+        }
+        t = sig;
+    }
+    if (!ok) {
+        double hi = alpha[0];  // the lowest eigenvalue is at most the Rayleigh quotient of e_1
+        for (int it = 0; it < 200 && hi - lo > 2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)); it++) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (sturm_below(m, alpha, b.data(), mid, tiny) >= 1) hi = mid;
+            else lo = mid;
+        }
+        t = 0.5 * (lo + hi);
+        for (int j = 0; j < m; j++) y[j] = 1.0 / sqrt((double)m);
+    }
+    for (int it = 0; it < (ok ? 1 : 3); it++) {
+        tridiag_shift_solve(m, alpha, b.data(), t, pivot_floor, y.data());
+        if (!normalise()) return HPHI_E_NUMERIC;
     }
     *theta = t;
     *ylast = fabs(y[m - 1]);
+    if (warm) *warm = t;
     return HPHI_OK;
+}
+
+int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, double *ylast) {
+    return lowest_ritz_warm(m, alpha, beta2, nullptr, theta, ylast);
 }
 
 namespace {
@@ -285,7 +350,7 @@ static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
     void *u = ctx->vec[0];
     std::vector<double> alpha_h(M + 1, 0.0), beta2_h(M + 2, 0.0), y;
     int steps = 0, conv = 0, brk = 0;
-    double theta = 0.0, resid_est = -1.0;
+    double theta = 0.0, resid_est = -1.0, warm = std::nan("");
     auto lincomb = [&](const void *x, const void *yv, void *out, const double *cdev, int red_oo) -> int {
         LinComb B{};
         B.real_dtype = dt;
@@ -359,7 +424,7 @@ static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
             if (flag > 0 && !(brk && mstop <= flag - 1))
                 return fail(set_err(ctx, HPHI_E_NUMERIC, "Lanczos: non-finite scalars at step %d", flag - 1));
             double yl = 0.0;
-            if ((st = lowest_ritz(mstop, alpha_h.data(), beta2_h.data(), &theta, &yl)))
+            if ((st = lowest_ritz_warm(mstop, alpha_h.data(), beta2_h.data(), &warm, &theta, &yl)))
                 return fail(set_err(ctx, st, "tridiagonal eigensolver failed"));
             resid_est = sqrt(beta2_h[mstop]) * yl;
             steps = mstop;
@@ -463,10 +528,12 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
     if ((st = launch_dot(ctx, dt, 0, D, 1, cur, 1, cur, 1, red))) return fail(st);
     k_lz<<<1, 32, 0, ctx->stream>>>(LZ_INIT, 0, red, alpha_d, beta2_d, coefA, coefB, ctx->dflag);
 
-    // convergence check: lowest Ritz value and the residual estimate
+    // convergence check: lowest Ritz value and the residual estimate (warm-started
+    // from the previous check's value, an upper bound of the new one)
+    double warm = std::nan("");
     auto solve_T = [&](int m) -> int {
         double yl = 0.0;
-        int s2 = lowest_ritz(m, alpha_h.data(), beta2_h.data(), &theta, &yl);
+        int s2 = lowest_ritz_warm(m, alpha_h.data(), beta2_h.data(), &warm, &theta, &yl);
         if (s2) return s2;
         resid_est = sqrt(beta2_h[m]) * yl;
         return HPHI_OK;

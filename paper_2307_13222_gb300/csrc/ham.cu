@@ -139,6 +139,8 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->aup);
     cudaFree(h->ll_pk);
     cudaFree(h->ja16);
+    cudaFree(h->dterms_d);
+    cudaFree(h->rowstate);
     delete h;
 }
 
@@ -179,6 +181,7 @@ int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) 
     for (auto &kv : pairs) {
         int i = kv.first.first, j = kv.first.second;
         double Jz = kv.second.first, Jxy = kv.second.second;
+        H->dterms.push_back(DTerm{DT_SPIN, i, j, 0, Jz, Jxy});
         c0 += 0.25 * Jz;
         if (j < nlo) {
             if (ncoef >= kMaxCoef) return set_err(ctx, HPHI_E_INVAL, "too many low-low bonds");
@@ -281,9 +284,13 @@ int build_hubbard(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_term
     D.ddn = B->sp[1].dim;
     std::vector<HopPair> hp[2];
     int ncoef = 0;
+    for (int i = 0; i < N; i++)
+        if (U[i] != 0.0) H->dterms.push_back(DTerm{DT_U, i, i, 0, U[i], 0.0});
+    for (auto &kv : vpairs) H->dterms.push_back(DTerm{DT_V, kv.first.first, kv.first.second, 0, kv.second, 0.0});
     for (auto &kv : hops) {
         if (kv.second == 0.0) continue;
         int s = std::get<0>(kv.first);
+        H->dterms.push_back(DTerm{DT_HOP, std::get<1>(kv.first), std::get<2>(kv.first), s, kv.second, 0.0});
         if (ncoef + 2 > kMaxCoef) return set_err(ctx, HPHI_E_INVAL, "too many hopping pairs");
         D.coef[ncoef] = -kv.second;     // sign +: -t
         D.coef[ncoef + 1] = kv.second;  // sign -: +t
@@ -365,6 +372,14 @@ extern "C" int hphi_build_hamiltonian(hphi_ctx *ctx, const hphi_basis *basis, co
         if (!st) {
             cudaError_t e = cudaMemcpy(H->desc, &H->host, sizeof(HamDesc), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = cuda_err(ctx, e, "descriptor copy");
+        }
+    }
+    if (!st) {
+        st = dev_alloc(ctx, &H->dterms_d, H->dterms.size() > 0 ? H->dterms.size() : 1);
+        if (!st && !H->dterms.empty()) {
+            cudaError_t e = cudaMemcpy(H->dterms_d, H->dterms.data(), sizeof(DTerm) * H->dterms.size(),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_err(ctx, e, "term list copy");
         }
     }
     // 16-bit copy of Lin's ja for the on-the-fly ranks of the H*x kernel

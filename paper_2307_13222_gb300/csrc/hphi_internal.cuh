@@ -62,6 +62,14 @@ struct VTerm {    // Hubbard V n_i n_j
     double v;
 };
 
+// The merged interaction list in plain form (one entry per bond / hop / U / V),
+// for the direct row evaluation of the small-problem solver.
+enum DTermKind { DT_SPIN = 0, DT_HOP = 1, DT_U = 2, DT_V = 3 };
+struct DTerm {
+    int kind, i, j, s;  // s: species of a hop (0 up, 1 down)
+    double a, b;        // spin: Jz, Jxy; hop: t; U: U; V: V
+};
+
 // Per-Hamiltonian descriptor (device copy read by every block at set-up).
 struct HamDesc {
     int model;
@@ -151,6 +159,11 @@ struct hphi_ham {
     uint32_t *ll_pk = nullptr;   // packed low-low lists (target | coefficient index << 24)
     uint16_t *ja16 = nullptr;    // Lin's ja as 16-bit ranks (spin sector, N_lo <= 16)
     int max_row_entries = 0;
+    // plain term list (host and device) and, for the S^z sector, the state of
+    // every row (built on first use by the small-problem solver)
+    std::vector<hphi::DTerm> dterms;
+    hphi::DTerm *dterms_d = nullptr;
+    uint32_t *rowstate = nullptr;
     // launch tuning (hphi_ham_set_tuning)
     int tune_inner = -1;
     int tune_split = 1;
@@ -244,6 +257,14 @@ int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V,
 int launch_maxpy(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const double *c_dev, void *w);
 int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x, int64_t ldx, void *y,
                 int64_t ldy);
+
+// ---- tridiagonal helpers (drivers.cu) ------------------------------------------------
+int tridiag_ql(int n, double *d, double *e, double *z);
+// lowest eigenvalue of the Lanczos tridiagonal T_m (alpha[0..m-1], beta2[1..m-1])
+// and |last component| of its normalised eigenvector
+int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, double *ylast);
+// the same with a warm start (an upper bound of the lowest eigenvalue, updated)
+int lowest_ritz_warm(int m, const double *alpha, const double *beta2, double *warm, double *theta, double *ylast);
 
 // ---- pattern (pattern.cu) --------------------------------------------------------
 int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,

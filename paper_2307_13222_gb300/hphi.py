@@ -52,6 +52,23 @@ class _KrylovResult(C.Structure):
     _fields_ = [("steps", C.c_int), ("converged", C.c_int), ("max_resid", C.c_double)]
 
 
+class _ServerOpts(C.Structure):
+    _fields_ = [("mem_budget", C.c_double), ("max_active", C.c_int), ("chunk", C.c_int),
+                ("small_max_dim", C.c_int64)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ham", C.c_void_p), ("seed", C.c_uint64), ("max_steps", C.c_int),
+                ("tol", C.c_double), ("q", C.c_double), ("eta", C.c_double), ("nz", C.c_int),
+                ("omega", C.c_void_p)]
+
+
+class _Reply(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("steps", C.c_int), ("krylov_steps", C.c_int),
+                ("lane", C.c_int), ("e0", C.c_double), ("max_resid", C.c_double), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
 _lib = None
 vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
 _SIGS = {
@@ -87,6 +104,13 @@ _SIGS = {
     "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
     "hphi_apply_sz_sum": (i32, [vp, vp, i32, vp, i64, vp, i64, vp]),
     "hphi_time_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_lanczos_batch": (i32, [vp, i32, vp, vp, vp, C.POINTER(_LanczosOpts), vp, vp]),
+    "hphi_server_create": (i32, [vp, C.POINTER(_ServerOpts), C.POINTER(vp)]),
+    "hphi_server_destroy": (None, [vp]),
+    "hphi_server_clock": (dbl, [vp]),
+    "hphi_server_submit": (i32, [vp, C.POINTER(_Request), C.POINTER(i64)]),
+    "hphi_server_step": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
+    "hphi_server_result": (i32, [vp, i64, C.POINTER(_Reply), vp]),
     "hphi_shifted_krylov": (i32, [vp, vp, C.POINTER(_KrylovOpts), i32, vp, i64, i32, vp, vp, vp, vp, vp,
                                   C.POINTER(_KrylovResult)]),
 }
@@ -367,6 +391,105 @@ def hphi_lanczos(ham: Hamiltonian, v0, max_steps: int, tol: float, check_every: 
     m = res.steps
     return dict(converged=st == HPHI_OK, status=st, e0=res.e0, resid_est=res.resid_est, resid=res.resid, steps=m,
                 breakdown=bool(res.breakdown), alpha=alpha[:m], beta=beta[1:m + 1])
+
+
+def hphi_lanczos_batch(hams, v0s, max_steps: int, tol: float, check_every: int = 8, gs_outs=None):
+    """Ground states of many small problems at once (FP64 CUDA start vectors).
+    Returns one dict per problem (as hphi_lanczos, plus its status)."""
+    n = len(hams)
+    if n == 0:
+        return []
+    ctx = hams[0].ctx
+    if len(v0s) != n or (gs_outs is not None and len(gs_outs) != n):
+        raise ValueError("one start vector (and ground-state buffer) per problem")
+    for h, v in zip(hams, v0s):
+        if not v.is_cuda or v.dtype.itemsize != 8 or v.is_complex() or v.dim() != 1 or v.stride(0) != 1:
+            raise ValueError("start vectors must be contiguous FP64 CUDA vectors")
+        if v.numel() != int(ctx.lib.hphi_ham_dim(h.h)):
+            raise ValueError("start vector length differs from the problem's dimension")
+    for h, g in zip(hams, gs_outs or []):
+        if g is not None and (not g.is_cuda or g.dtype.itemsize != 8 or g.is_complex() or not g.is_contiguous()
+                              or g.numel() != int(ctx.lib.hphi_ham_dim(h.h))):
+            raise ValueError("ground-state buffers must be contiguous FP64 CUDA vectors of the problem's length")
+    hs = (vp * n)(*[h.h for h in hams])
+    vs = (vp * n)(*[C.c_void_p(v.data_ptr()) for v in v0s])
+    gs = (vp * n)(*[C.c_void_p(g.data_ptr()) if g is not None else None for g in gs_outs]) if gs_outs else None
+    opts = _LanczosOpts(max_steps, tol, F64, check_every, 0)
+    res = (_LanczosResult * n)()
+    stat = (C.c_int * n)()
+    ctx._sync_stream()
+    st = ctx.lib.hphi_lanczos_batch(ctx.h, n, hs, vs, gs, C.byref(opts), res, stat)
+    if st != HPHI_OK and st not in list(stat):  # a call-level error, not a per-problem status
+        ctx.check(st)
+    return [dict(status=stat[p], converged=stat[p] == HPHI_OK, e0=res[p].e0, resid_est=res[p].resid_est,
+                 resid=res[p].resid, steps=res[p].steps, breakdown=bool(res[p].breakdown)) for p in range(n)]
+
+
+class Server:
+    """Continuous-batching server of ground-state and spectrum requests
+    (hphi_server_*).  Hamiltonians passed to submit() must outlive their
+    requests; the server keeps a reference to them."""
+
+    GROUND, SPECTRUM = 0, 1
+
+    def __init__(self, ctx: Context, mem_budget: float, max_active: int = 0, chunk: int = 0, small_max_dim: int = 0):
+        self.ctx = ctx
+        o = _ServerOpts(float(mem_budget), max_active, chunk, small_max_dim)
+        h = vp()
+        ctx._sync_stream()
+        ctx.check(ctx.lib.hphi_server_create(ctx.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def clock(self) -> float:
+        return float(self.ctx.lib.hphi_server_clock(self.h))
+
+    def submit(self, ham: Hamiltonian, kind: int = 0, seed: int = 1, max_steps: int = 500, tol: float = 1e-10,
+               q: float = 0.0, eta: float = 0.05, omega=None) -> int:
+        om = np.ascontiguousarray(np.asarray(omega if omega is not None else [], dtype=np.float64))
+        r = _Request(kind, ham.h, seed, max_steps, tol, q, eta, om.size, _np(om) if om.size else None)
+        rid = i64(0)
+        self.ctx._sync_stream()
+        self.ctx.check(self.ctx.lib.hphi_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = (ham, om.size)
+        return rid.value
+
+    def step(self):
+        """One scheduling step; returns (running, queued)."""
+        a, b = i32(0), i32(0)
+        self.ctx.check(self.ctx.lib.hphi_server_step(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def result(self, rid: int):
+        rep = _Reply()
+        nz = self._keep[rid][1]
+        d = np.zeros(2 * max(nz, 1))
+        self.ctx.check(self.ctx.lib.hphi_server_result(self.h, rid, C.byref(rep), _np(d)))
+        out = {k: getattr(rep, k) for k, _ in _Reply._fields_}
+        out["done"] = bool(out["done"])
+        out["D"] = (d[0::2] + 1j * d[1::2])[:nz] if nz else None
+        return out
+
+    def run_until_done(self, ids, max_steps: int = 1000000):
+        for _ in range(max_steps):
+            if all(self.result(i)["done"] for i in ids):
+                return
+            running, queued = self.step()
+            if running == 0 and queued == 0 and not all(self.result(i)["done"] for i in ids):
+                import time
+                time.sleep(0.001)  # the grid lane's worker still runs
+        raise RuntimeError("server did not finish")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.hphi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hphi_tpq_step(ham: Hamiltonian, V, dtau: float, nmax: int, norm2: np.ndarray):
