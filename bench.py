@@ -660,7 +660,140 @@ def run_szz(args):
     return _finish(line, rank, dist, ctx)
 
 
-WORKLOADS = {"chain16": run_chain16, "hubbard4x4": run_hubbard4x4, "ctpq26": run_ctpq26, "szz": run_szz}
+def run_serve(args):
+    """Serving mix: seeded Poisson arrivals (seed 5) of requests, half ground
+    states (residual 1e-10) and half S^zz(q, w) spectra (200 shifts w in
+    [0, 4] above E0, eta = 0.05, every shift's relative residual <= 1e-6,
+    q = 2 pi m / L with seeded m); models drawn from Heisenberg chains and
+    2-leg ladders with J_b ~ U[0.5, 1.5] and half-filled Hubbard 2 x L
+    clusters with U ~ U[4, 10].  Sizes are capped (N <= 22, 2 x 6) so that a
+    trace ends in about a minute; all of them run on the batched block lane.
+    One step = 16 requests of the trace; value = completed requests / s."""
+    import torch
+    import numpy as np
+    from paper_2307_13222_gb300 import hphi
+    from workloads import chain, ladder, heisenberg_terms, hubbard_terms, uniform_couplings
+    world, rank, local, dist, ctx = _setup(args)
+    rng = np.random.default_rng(5)
+    R = 16 * args.steps
+    rate = 40.0  # requests per second
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
+    reqs, hams = [], {}
+    for i in range(R):
+        fam = rng.integers(0, 3)
+        if fam == 0:
+            N = int(rng.choice([18, 20, 22]))
+            key = ("chain", N, int(rng.integers(0, 4)))
+            terms = heisenberg_terms(chain(N), uniform_couplings(N, 0.5, 1.5, 100 + key[2]))
+            model, nu, nd, L = "SPIN_HALF", N // 2, 0, N
+        elif fam == 1:
+            N = int(rng.choice([18, 20, 22]))
+            key = ("ladder", N, int(rng.integers(0, 4)))
+            bonds = ladder(N // 2)
+            terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 200 + key[2]))
+            model, nu, nd, L = "SPIN_HALF", N // 2, 0, N // 2
+        else:
+            Lh = int(rng.choice([4, 5, 6]))
+            U = float(rng.uniform(4.0, 10.0))
+            key = ("hubbard", Lh, round(U, 6))
+            N = 2 * Lh
+            terms = hubbard_terms(N, ladder(Lh), t=1.0, U=U)
+            model, nu, nd, L = "HUBBARD", Lh, Lh, Lh
+        if key not in hams:
+            b = hphi.Basis(ctx, model, N, nu, nd)
+            hams[key] = (b, hphi.Hamiltonian(ctx, b, terms), L)
+        kind = int(rng.integers(0, 2))
+        q = 2 * np.pi * int(rng.integers(1, hams[key][2] // 2 + 1)) / hams[key][2]
+        reqs.append((arrivals[i], key, kind, int(1000 + i), q))
+    omega = np.linspace(0.0, 4.0, 200)
+    srv = hphi.Server(ctx, 60e9, chunk=16)
+    # warm-up: the smallest request of each kind
+    w_ids = [srv.submit(hams[reqs[0][1]][1], kind=k, seed=7, max_steps=3000, tol=1e-10 if k == 0 else 1e-6,
+                        q=reqs[0][4], eta=0.05, omega=omega) for k in (0, 1)]
+    srv.run_until_done(w_ids)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start = srv.clock()
+    ids, nsub, steps = [], 0, 0
+    while True:
+        now = srv.clock() - t_start
+        while nsub < R and reqs[nsub][0] <= now:
+            a, key, kind, seed, q = reqs[nsub]
+            ids.append((srv.submit(hams[key][1], kind=kind, seed=seed, max_steps=3000,
+                                   tol=1e-10 if kind == 0 else 1e-6, q=q, eta=0.05, omega=omega), a))
+            nsub += 1
+        running, queued = srv.step()
+        steps += 1
+        if nsub == R and running == 0 and queued == 0:
+            break
+        if running == 0 and queued == 0 and nsub < R:
+            time.sleep(max(0.0, min(0.01, reqs[nsub][0] - (srv.clock() - t_start))))
+    t_end = srv.clock() - t_start
+    ck = clocks.stop()
+    res = [srv.result(i) for i, _ in ids]
+    lat = [r["t_done"] - t_start - a for r, (i, a) in zip(res, ids)]
+    ok = sum(r["status"] == 0 for r in res)
+    ms = max_over_ranks(t_end * 1e3, dist)
+    kinds = [reqs[j][2] for j in range(R)]
+    line = _base(args, world, "served_requests_per_s", world * R / (ms * 1e-3), "requests/s", ms / args.steps, "f64",
+                 {"workload": "serving_mix_poisson", "requests": R, "arrival_rate_per_s": rate,
+                  "ground_fraction": 1.0 - float(np.mean(kinds)), "shifts": 200, "eta": 0.05,
+                  "models": "chains/ladders N in {18,20,22}, Hubbard 2xL L in {4,5,6}",
+                  "form": "continuous batching, one block per recurrence", "parallelism": f"replicas{world}",
+                  "l2": "per-request working sets 0.4-40 MB, distinct per request (no flush)"})
+    line.update({"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                 "completed_ok": ok, "server_steps": steps,
+                 "roofline": None, "gpu_launches": steps,
+                 "e2e": {"value": world * R / (ms * 1e-3), "unit": "requests/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 16 * 200 * 16}})
+    if ck:
+        line["clocks"] = ck
+    srv.close()
+    return _finish(line, rank, dist, ctx)
+
+
+def run_apply(args):
+    """Plain H*x (hphi_apply_H, x -> y) on the S^z=0 sector of a periodic
+    square lattice Lx x Ly (--lattice, e.g. 6x5 or 8x4), one column: the case
+    used for kernel captures.  value = algorithmic GB/s (read x + write y)."""
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    from workloads import square, heisenberg_terms
+    world, rank, local, dist, ctx = _setup(args)
+    Lx, Ly = (int(v) for v in args.lattice.lower().split("x"))
+    N = Lx * Ly
+    b = hphi.Basis(ctx, "SPIN_HALF", N, N // 2)
+    h = hphi.Hamiltonian(ctx, b, heisenberg_terms(square(Lx, Ly), 1.0))
+    if args.variant is not None:
+        h.set_tuning(variant=args.variant)
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    x = torch.empty(b.dim, dtype=tdt, device="cuda")
+    hphi.hphi_random_vector(ctx, x, 1)
+    y = torch.empty_like(x)
+    for _ in range(max(args.warmup, 1)):
+        hphi.hphi_apply_H(h, x, y)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        hphi.hphi_apply_H(h, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    es = 4 if tdt == torch.float32 else 8
+    line = _base(args, world, "hv_gbps", job_gbps(world, args.steps * 2.0 * es * b.dim, ms), "GB/s", ms / args.steps,
+                 args.dtype, {"workload": f"heisenberg_square_{Lx}x{Ly}_Sz0_apply", "dim": b.dim,
+                              "variant": h.get_tuning()["variant"], "parallelism": f"replicas{world}",
+                              "l2": "vector of %.2f GB > L2" % (es * b.dim / 1e9)})
+    line.update({"roofline": _roofline(ctx, 2.0 * es * b.dim, "single-column H*x"), "gpu_launches": args.steps})
+    return _finish(line, rank, dist, ctx)
+
+
+WORKLOADS = {"chain16": run_chain16, "hubbard4x4": run_hubbard4x4, "ctpq26": run_ctpq26, "szz": run_szz,
+             "serve": run_serve, "apply": run_apply}
 
 
 def main():
@@ -673,6 +806,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the extra FP64 measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", default="6x5", help="apply workload: Lx x Ly of the square lattice")
+    ap.add_argument("--variant", type=int, default=None, help="apply workload: H*x kernel variant (-1, 0, 1, 2)")
     ap.add_argument("--workload", choices=["square4x8"] + sorted(WORKLOADS), default="square4x8",
                     help="square4x8 (default): Lanczos steps on the 4x8 sector; the others measure the "
                          "remaining workloads (one JSON line each)")
