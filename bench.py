@@ -667,7 +667,8 @@ def run_serve(args):
     q = 2 pi m / L with seeded m); models drawn from Heisenberg chains and
     2-leg ladders with J_b ~ U[0.5, 1.5] and half-filled Hubbard 2 x L
     clusters with U ~ U[4, 10].  Sizes are capped (N <= 22, 2 x 6) so that a
-    trace ends in about a minute; all of them run on the batched block lane.
+    trace ends in about a minute; problems up to 2^17 rows run on the batched
+    block lane, larger ones on the grid lane (two workers).
     One step = 16 requests of the trace; value = completed requests / s."""
     import torch
     import numpy as np
@@ -727,8 +728,11 @@ def run_serve(args):
         steps += 1
         if nsub == R and running == 0 and queued == 0:
             break
-        if running == 0 and queued == 0 and nsub < R:
-            time.sleep(max(0.0, min(0.01, reqs[nsub][0] - (srv.clock() - t_start))))
+        st = srv.stats()
+        if st["block_running"] == 0 and st["queued"] == 0:
+            # nothing on the block lane: wait for the next arrival or the grid lane
+            nxt = reqs[nsub][0] - (srv.clock() - t_start) if nsub < R else 0.0005
+            time.sleep(max(0.0, min(0.0005, nxt)))
     t_end = srv.clock() - t_start
     ck = clocks.stop()
     res = [srv.result(i) for i, _ in ids]
@@ -740,11 +744,17 @@ def run_serve(args):
                  {"workload": "serving_mix_poisson", "requests": R, "arrival_rate_per_s": rate,
                   "ground_fraction": 1.0 - float(np.mean(kinds)), "shifts": 200, "eta": 0.05,
                   "models": "chains/ladders N in {18,20,22}, Hubbard 2xL L in {4,5,6}",
-                  "form": "continuous batching, one block per recurrence", "parallelism": f"replicas{world}",
+                  "form": "continuous batching: block lane (D <= 2^17, one block per recurrence) + grid lane",
+                  "parallelism": f"replicas{world}",
                   "l2": "per-request working sets 0.4-40 MB, distinct per request (no flush)"})
+    lanes = [r["lane"] for r in res]
+    sst = srv.stats()
     line.update({"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
-                 "completed_ok": ok, "server_steps": steps,
-                 "roofline": None, "gpu_launches": steps,
+                 "completed_ok": ok, "server_steps": steps, "grid_lane_requests": int(sum(lanes)),
+                 "roofline": None,
+                 # block-lane launches counted by the server; the grid lane's drivers launch
+                 # about 7 kernels per Lanczos step besides
+                 "gpu_launches": int(sst["block_launches"]), "arena_peak_gb": sst["arena_peak"] / 1e9,
                  "e2e": {"value": world * R / (ms * 1e-3), "unit": "requests/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 16 * 200 * 16}})
     if ck:

@@ -314,8 +314,8 @@ HPHI_API int hphi_lanczos_batch(hphi_ctx *ctx, int nprob, hphi_ham *const *hams,
  * of all of them at once, then evaluates each stopping rule after every step,
  * retires finished requests (freeing their memory at once) and admits queued
  * ones (FIFO) whose workspace fits and for which block slots are free.
- * Larger problems go to a second lane: a worker thread that runs the
- * grid-wide drivers on its own CUDA stream, concurrently.  A request's result
+ * Larger problems go to a second lane: worker threads that run the
+ * grid-wide drivers, each on its own CUDA stream, concurrently.  A request's result
  * does not depend on the other requests (bit for bit).
  * Requests: HPHI_REQ_GROUND, the ground-state energy (hphi_lanczos' recurrence
  * and stopping rule, FP64, Philox start vector of `seed`, residual `tol`);
@@ -334,7 +334,8 @@ typedef struct hphi_server_opts {
     double mem_budget;     /* bytes of the device arena */
     int max_active;        /* recurrences (thread blocks) at once; 0: 2 x SMs */
     int chunk;             /* Lanczos steps per server step; 0: 16 */
-    int64_t small_max_dim; /* larger problems use the grid lane; 0: 2^20 */
+    int64_t small_max_dim; /* larger problems use the grid lane; 0: 2^17 */
+    int grid_workers;      /* grid-lane worker threads, each with its own stream; 0: 2 */
 } hphi_server_opts;
 
 #define HPHI_REQ_GROUND 0
@@ -363,6 +364,16 @@ HPHI_API double hphi_server_clock(const hphi_server *server);
 HPHI_API int hphi_server_submit(hphi_server *server, const hphi_request *request, int64_t *id);
 HPHI_API int hphi_server_step(hphi_server *server, int *n_running, int *n_queued);
 HPHI_API int hphi_server_result(hphi_server *server, int64_t id, hphi_reply *reply, double *d_out);
+
+/* Counters of a server: kernel launches of the block lane (steps, vector
+ * passes, excitations, start vectors), requests finished per lane, requests
+ * running per lane and queued, arena bytes in use and at most. */
+typedef struct hphi_server_stats {
+    int64_t block_launches, block_done, grid_done;
+    int block_running, grid_running, queued;
+    double arena_used, arena_peak;
+} hphi_server_stats;
+HPHI_API int hphi_server_get_stats(hphi_server *server, hphi_server_stats *stats);
 
 /* ---- canonical TPQ step (Sec. 3.5.1) -----------------------------------------
  * One step Phi_{k+1} = U_c(dtau) Phi_k, U_c = sum_{n<=nmax} (-dtau H/2)^n / n!,

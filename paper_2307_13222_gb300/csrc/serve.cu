@@ -152,12 +152,15 @@ struct hphi_server {
     double *stage = nullptr, *stage_h = nullptr;
     int cap = 0;
     // grid lane
-    std::thread worker;
+    std::vector<std::thread> workers;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request *> grid_queue;
     bool stop = false;
     int grid_busy = 0;
+    // counters
+    int64_t launches = 0, grid_done = 0, block_done = 0;
+    size_t arena_used = 0, arena_peak = 0;
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
@@ -392,6 +395,7 @@ void grid_worker(hphi_server *S) {
         q->t_done = S->now();
         q->phase = PH_DONE;
         S->grid_busy--;
+        S->grid_done++;
     }
     if (gc) hphi_ctx_destroy(gc);
     if (st) cudaStreamDestroy(st);
@@ -403,7 +407,8 @@ extern "C" int hphi_server_create(hphi_ctx *ctx, const hphi_server_opts *opts, h
     if (!ctx || !opts || !out) return HPHI_E_INVAL;
     ctx->err.clear();
     *out = nullptr;
-    if (!(opts->mem_budget > 0) || opts->max_active < 0 || opts->chunk < 0 || opts->small_max_dim < 0)
+    if (!(opts->mem_budget > 0) || opts->max_active < 0 || opts->chunk < 0 || opts->small_max_dim < 0 ||
+        opts->grid_workers < 0 || opts->grid_workers > 16)
         return set_err(ctx, HPHI_E_INVAL, "server options");
     HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
     std::unique_ptr<hphi_server> S(new (std::nothrow) hphi_server());
@@ -412,7 +417,8 @@ extern "C" int hphi_server_create(hphi_ctx *ctx, const hphi_server_opts *opts, h
     S->opts = *opts;
     if (S->opts.max_active == 0) S->opts.max_active = 2 * ctx->sm_count;
     if (S->opts.chunk == 0) S->opts.chunk = 16;
-    if (S->opts.small_max_dim == 0) S->opts.small_max_dim = (int64_t)1 << 20;
+    if (S->opts.small_max_dim == 0) S->opts.small_max_dim = (int64_t)1 << 17;
+    if (S->opts.grid_workers == 0) S->opts.grid_workers = 2;
     int st = S->arena.init(ctx, (size_t)opts->mem_budget);
     if (st) return st;
     S->cap = S->opts.max_active;
@@ -427,7 +433,7 @@ extern "C" int hphi_server_create(hphi_ctx *ctx, const hphi_server_opts *opts, h
     }
     S->t0 = Clock::now();
     hphi_server *raw = S.release();
-    raw->worker = std::thread(grid_worker, raw);
+    for (int w = 0; w < raw->opts.grid_workers; w++) raw->workers.emplace_back(grid_worker, raw);
     *out = raw;
     return HPHI_OK;
 }
@@ -439,7 +445,8 @@ extern "C" void hphi_server_destroy(hphi_server *S) {
         S->stop = true;
     }
     S->cv.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    for (auto &w : S->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(S->ctx->device);
     cudaStreamSynchronize(S->ctx->stream);
     cudaFree(S->dprob);
@@ -518,6 +525,9 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
         double *v0 = q->base;
         double *ws = v0 + h->D;
         if ((st = hphi_random_vector(ctx, HPHI_F64, h->D, 1, q->r.seed, v0, 1))) return st;
+        S->launches++;
+        S->arena_used += q->bytes;
+        S->arena_peak = S->arena_used > S->arena_peak ? S->arena_used : S->arena_peak;
         q->ground.reset(new Task());
         init_task(*q->ground, q, ROLE_GROUND, ws, v0, 1, M);
         HPHI_CUDA(ctx, cudaMemsetAsync(q->ground->P.state, 0, 2 * sizeof(int), ctx->stream));
@@ -543,6 +553,7 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
         HPHI_CUDA(ctx, cudaMemcpyAsync(S->dprob, gsd.data(), sizeof(BProb) * gsd.size(), cudaMemcpyHostToDevice,
                                        ctx->stream));
         if ((st = batch_launch_gs(ctx, S->dprob, (int)gsd.size(), gsdyn))) return st;
+        S->launches++;
         // the descriptors are read by the launch before the next upload (same stream)
         for (Request *q : S->running) {
             if (q->phase != PH_GSPASS) continue;
@@ -552,6 +563,7 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
             bool im = false;
             weights_of(q, w, &im);
             if ((st = hphi_apply_sz_sum(ctx, h->basis, HPHI_F64, q->gs, 1, q->ex, 2, w.data()))) return st;
+            S->launches++;
             double *kws = q->ex + 2 * h->D;
             for (int c = 0; c < (im ? 2 : 1); c++) {
                 std::unique_ptr<Task> t(new Task());
@@ -589,6 +601,7 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
         }
         HPHI_CUDA(ctx, cudaMemcpyAsync(S->dprob, d.data(), sizeof(BProb) * n, cudaMemcpyHostToDevice, ctx->stream));
         if ((st = batch_launch_steps(ctx, S->dprob, n, dyn))) return st;
+        S->launches++;
         const size_t sn = (size_t)n * (3 + 2 * (size_t)M_cap);
         HPHI_CUDA(ctx, cudaMemcpyAsync(S->stage_h, S->stage, sizeof(double) * sn, cudaMemcpyDeviceToHost, ctx->stream));
         HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -639,6 +652,8 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
             q->phase = PH_DONE;
             q->t_done = S->now();
             S->arena.release(q->off, q->bytes);
+            S->arena_used -= q->bytes;
+            S->block_done++;
             q->ground.reset();
             q->kry.clear();
         } else {
@@ -651,6 +666,20 @@ extern "C" int hphi_server_step(hphi_server *S, int *n_running, int *n_queued) {
         *n_running = (int)S->running.size() + S->grid_busy;
     }
     if (n_queued) *n_queued = (int)S->queue.size();
+    return HPHI_OK;
+}
+
+extern "C" int hphi_server_get_stats(hphi_server *S, hphi_server_stats *out) {
+    if (!S || !out) return HPHI_E_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->block_launches = S->launches;
+    out->block_done = S->block_done;
+    out->grid_done = S->grid_done;
+    out->block_running = (int)S->running.size();
+    out->grid_running = S->grid_busy;
+    out->queued = (int)S->queue.size();
+    out->arena_used = (double)S->arena_used;
+    out->arena_peak = (double)S->arena_peak;
     return HPHI_OK;
 }
 

@@ -54,7 +54,7 @@ class _KrylovResult(C.Structure):
 
 class _ServerOpts(C.Structure):
     _fields_ = [("mem_budget", C.c_double), ("max_active", C.c_int), ("chunk", C.c_int),
-                ("small_max_dim", C.c_int64)]
+                ("small_max_dim", C.c_int64), ("grid_workers", C.c_int)]
 
 
 class _Request(C.Structure):
@@ -67,6 +67,12 @@ class _Reply(C.Structure):
     _fields_ = [("done", C.c_int), ("status", C.c_int), ("steps", C.c_int), ("krylov_steps", C.c_int),
                 ("lane", C.c_int), ("e0", C.c_double), ("max_resid", C.c_double), ("t_submit", C.c_double),
                 ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("block_launches", C.c_int64), ("block_done", C.c_int64), ("grid_done", C.c_int64),
+                ("block_running", C.c_int), ("grid_running", C.c_int), ("queued", C.c_int),
+                ("arena_used", C.c_double), ("arena_peak", C.c_double)]
 
 
 _lib = None
@@ -111,6 +117,7 @@ _SIGS = {
     "hphi_server_submit": (i32, [vp, C.POINTER(_Request), C.POINTER(i64)]),
     "hphi_server_step": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "hphi_server_result": (i32, [vp, i64, C.POINTER(_Reply), vp]),
+    "hphi_server_get_stats": (i32, [vp, C.POINTER(_ServerStats)]),
     "hphi_shifted_krylov": (i32, [vp, vp, C.POINTER(_KrylovOpts), i32, vp, i64, i32, vp, vp, vp, vp, vp,
                                   C.POINTER(_KrylovResult)]),
 }
@@ -432,9 +439,10 @@ class Server:
 
     GROUND, SPECTRUM = 0, 1
 
-    def __init__(self, ctx: Context, mem_budget: float, max_active: int = 0, chunk: int = 0, small_max_dim: int = 0):
+    def __init__(self, ctx: Context, mem_budget: float, max_active: int = 0, chunk: int = 0, small_max_dim: int = 0,
+                 grid_workers: int = 0):
         self.ctx = ctx
-        o = _ServerOpts(float(mem_budget), max_active, chunk, small_max_dim)
+        o = _ServerOpts(float(mem_budget), max_active, chunk, small_max_dim, grid_workers)
         h = vp()
         ctx._sync_stream()
         ctx.check(ctx.lib.hphi_server_create(ctx.h, C.byref(o), C.byref(h)))
@@ -470,14 +478,20 @@ class Server:
         out["D"] = (d[0::2] + 1j * d[1::2])[:nz] if nz else None
         return out
 
+    def stats(self) -> dict:
+        st = _ServerStats()
+        self.ctx.check(self.ctx.lib.hphi_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
     def run_until_done(self, ids, max_steps: int = 1000000):
         for _ in range(max_steps):
             if all(self.result(i)["done"] for i in ids):
                 return
-            running, queued = self.step()
-            if running == 0 and queued == 0 and not all(self.result(i)["done"] for i in ids):
+            self.step()
+            st = self.stats()
+            if st["block_running"] == 0 and st["queued"] == 0:
                 import time
-                time.sleep(0.001)  # the grid lane's worker still runs
+                time.sleep(0.0005)  # only the grid lane's workers run
         raise RuntimeError("server did not finish")
 
     def close(self):
