@@ -459,6 +459,16 @@ HPHI_API int hphi_shifted_krylov(hphi_ctx *ctx, const hphi_ham *ham, const hphi_
                                  double *resid_host, double *alpha_host, double *beta_host,
                                  hphi_krylov_result *result);
 
+/* ---- microcanonical TPQ step (Sec. 3.5.1) ---------------------------------------
+ * Phi_{k+1} = U_m Phi_k, U_m = 1 - (dtau/2) H with dtau = 2 / (l n_sites): the
+ * cTPQ step above with nmax = 1 (same arguments, layout and outputs).  The
+ * inverse temperature of the state the step starts from is
+ * beta_k = k dtau / (1 - u_k / l), u_k = e_host[q] / n_sites; l must exceed
+ * the largest eigenvalue of H / n_sites for U_m to be positive on the spectrum.
+ * HPHI_E_INVAL for l <= 0 or n_sites < 1. */
+HPHI_API int hphi_mtpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv, double l,
+                            int n_sites, double *norm2_inout, double *e_host, double *h2_host, double *logd_host);
+
 /* ---- host utility: symmetric tridiagonal eigenproblem ------------------------
  * All eigenvalues (ascending) of the n x n tridiagonal with diagonal a[0..n-1]
  * and off-diagonal b[1..n-1] (b[k] couples rows k-1 and k; b[0] unused), by the

@@ -726,6 +726,19 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
     return HPHI_OK;
 }
 
+// Microcanonical TPQ (Sec. 3.5.1): U_m = 1 - (dtau / 2) H with dtau = 2 / (l N_s),
+// i.e. the cTPQ step with nmax = 1; the caller forms beta_k = k dtau / (1 - u_k / l)
+// from u_k = e / N_s of the state the step starts from.
+extern "C" int hphi_mtpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv,
+                              double l, int n_sites, double *norm2_inout, double *e_out, double *h2_out,
+                              double *logd_out) {
+    if (!ctx || !ham) return HPHI_E_INVAL;
+    if (!(l > 0.0) || !isfinite(l) || n_sites < 1)
+        return set_err(ctx, HPHI_E_INVAL, "mTPQ needs l > 0 and n_sites >= 1");
+    return hphi_tpq_step(ctx, ham, dtype, nvec, V, ldv, 2.0 / (l * (double)n_sites), 1, norm2_inout, e_out, h2_out,
+                         logd_out);
+}
+
 extern "C" int hphi_tpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv,
                              double dtau, int nmax, double *norm2, double *e_out, double *h2_out, double *logd_out) {
     if (!ctx || !ham || !V || !norm2 || !e_out || !h2_out || !logd_out) return HPHI_E_INVAL;

@@ -106,6 +106,7 @@ _SIGS = {
     "hphi_random_vector": (i32, [vp, i32, i64, i32, C.c_uint64, vp, i64]),
     "hphi_lanczos": (i32, [vp, vp, C.POINTER(_LanczosOpts), vp, vp, vp, vp, C.POINTER(_LanczosResult)]),
     "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_mtpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
     "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
     "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
     "hphi_apply_sz_sum": (i32, [vp, vp, i32, vp, i64, vp, i64, vp]),
@@ -618,6 +619,25 @@ def hphi_szz_spectrum(ham: Hamiltonian, basis: Basis, gs, qs, z, max_steps: int,
     r = hphi_shifted_krylov(ham, rhs, z, max_steps, tol, check_every)
     Dq = np.stack([r["G"][col[k]] + (r["G"][col[k] + 1] if two[k] else 0.0) for k in range(nq)])
     return -Dq.imag, Dq, r
+
+
+def hphi_mtpq_step(ham: Hamiltonian, V, l: float, n_sites: int, norm2: np.ndarray):
+    """One microcanonical TPQ step in place on V (U_m = 1 - H / (l N_s)); norm2
+    is updated in place.  Returns (e, h2, logd) of the state before the step."""
+    ctx = ham.ctx
+    pv, nv, ld = _vec(V)
+    assert norm2.dtype == np.float64 and norm2.size == nv and norm2.flags.c_contiguous
+    e, h2, logd = np.zeros(nv), np.zeros(nv), np.zeros(nv)
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_mtpq_step(ctx.h, ham.h, _dtype_code(V), nv, pv, ld, float(l), int(n_sites), _np(norm2),
+                                     _np(e), _np(h2), _np(logd)))
+    return e, h2, logd
+
+
+def mtpq_beta(k: int, l: float, n_sites: int, e) -> np.ndarray:
+    """beta_k = k dtau / (1 - u_k / l), dtau = 2 / (l N_s), u_k = e / N_s (Sec. 3.5.1)."""
+    dtau = 2.0 / (l * n_sites)
+    return k * dtau / (1.0 - np.asarray(e) / n_sites / l)
 
 
 def hphi_dump_pattern(ham: Hamiltonian, row0: int, row1: int):

@@ -67,3 +67,22 @@ def test_tpq_block_of_16_complex_vectors(coop, dtype):
         assert np.allclose(e, eo, rtol=tol, atol=tol), (step, e, eo)
         assert np.allclose(h2, h2o, rtol=tol), step
         assert np.allclose(logd, np.log(do), rtol=tol, atol=tol), step
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex64])
+def test_mtpq_steps_match_oracle(dtype):
+    """mTPQ step = cTPQ step with nmax = 1 and dtau = 2 / (l N_s)."""
+    N, l = 10, 1.8
+    m, b, h = pair("SPIN_HALF_GC", N, 0, 0, _model(N, 4))
+    cplx = dtype.is_complex
+    V0 = random_vectors(m.dim, 4, 31, complex_=cplx)
+    Vg = torch.from_numpy(V0).to(dtype).cuda().contiguous()
+    Vo = Vg.cpu().numpy().astype(np.complex128 if cplx else np.float64).copy()
+    norm2 = np.zeros(4)
+    tol = 1e-11 if dtype == torch.float64 else 2e-5
+    for step in range(20):
+        e, h2, logd = hphi.hphi_mtpq_step(h, Vg, l, N, norm2)
+        eo, h2o, do = m.tpq_step(Vo, 2.0 / (l * N), 1)
+        assert np.allclose(e, eo, rtol=tol, atol=tol) and np.allclose(logd, np.log(do), rtol=tol, atol=tol), step
+        beta = hphi.mtpq_beta(step, l, N, e)
+        assert np.allclose(beta, step * (2.0 / (l * N)) / (1.0 - eo / N / l), rtol=tol, atol=tol)

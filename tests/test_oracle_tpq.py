@@ -96,3 +96,47 @@ def test_bootstrap_identical_samples_have_zero_spread():
     bs = O.bootstrap_tpq(E, E2, logn, P=8, M=4, seed=0)
     assert np.allclose(bs["H"][0], E[0]) and np.allclose(bs["H"][1], 0)
     assert np.allclose(bs["fluct"][0], 0.1)
+
+
+def test_mtpq_step_is_the_first_order_operator():
+    """mTPQ (Sec. 3.5.1): U_m = 1 - (dtau/2) H with dtau = 2/(l N_s) is the
+    cTPQ step with nmax = 1; checked against the dense operator."""
+    import numpy as np
+    import oracle as O
+    from workloads import chain, heisenberg_terms, random_vectors
+    N, l = 8, 2.0
+    m = O.Model("SPIN_HALF_GC", N, 0, 0, heisenberg_terms(chain(N), 1.0))
+    H = O.dense_matrix(m)
+    V = np.ascontiguousarray(random_vectors(m.dim, 3, 4))
+    V0 = V.copy()
+    dtau = 2.0 / (l * N)
+    e, h2, d = m.tpq_step(V, dtau, 1)
+    for q in range(3):
+        w = V0[:, q] - H @ V0[:, q] / (l * N)
+        assert np.allclose(V[:, q], w / np.linalg.norm(w), rtol=0, atol=1e-14)
+        assert d[q] == np.dot(w, w) / np.dot(V0[:, q], V0[:, q]) or abs(d[q] - np.dot(w, w) / np.dot(V0[:, q], V0[:, q])) < 1e-14
+
+
+def test_mtpq_temperature_follows_the_canonical_energy():
+    """u_k = <H>_k / N_s at beta_k = k dtau / (1 - u_k / l) tracks the canonical
+    energy per site of the dense spectrum (16 vectors, 2^12 states) up to the
+    typicality and microcanonical-versus-canonical finite-size differences
+    (a few percent of the bandwidth at N_s = 12)."""
+    import numpy as np
+    import oracle as O
+    from workloads import random_regular_graph, uniform_couplings, heisenberg_terms, random_vectors
+    N, l = 12, 1.5
+    bonds = random_regular_graph(N, 3, 6)
+    m = O.Model("SPIN_HALF_GC", N, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 7)))
+    E = np.linalg.eigvalsh(O.dense_matrix(m))
+    assert E.max() / N < l
+    V = np.ascontiguousarray(random_vectors(m.dim, 16, 8))
+    dtau = 2.0 / (l * N)
+    for k in range(400):
+        e, h2, d = m.tpq_step(V, dtau, 1)
+        if k in (50, 150, 399):
+            u = e / N
+            beta = k * dtau / (1.0 - u / l)
+            for b_, u_ in zip(beta, u):
+                ec, _ = O.canonical_thermo(E, np.array([1.0 / b_]))
+                assert abs(u_ - ec[0] / N) < 0.05, (k, u_, ec[0] / N)
