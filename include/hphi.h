@@ -459,6 +459,20 @@ HPHI_API int hphi_shifted_krylov(hphi_ctx *ctx, const hphi_ham *ham, const hphi_
                                  double *resid_host, double *alpha_host, double *beta_host,
                                  hphi_krylov_result *result);
 
+/* ---- LOBPCG (Sec. 3.3) -------------------------------------------------------------
+ * hphi_lobpcg: the m lowest eigenpairs (1 <= m <= 32) of H by the locally
+ * optimal block conjugate gradient method (no preconditioner): each
+ * iteration one block H*V of the residuals and a Rayleigh-Ritz step on
+ * [R, Phi, P].  X: device FP64 [D][m] (leading dimension m), in: the start
+ * block (full rank), out: the Ritz vectors (orthonormal columns).  Stops when
+ * every residual |H x_n - e_n x_n| <= tol max(1, |e_n|), or after max_iter
+ * iterations (HPHI_E_NOTCONV, outputs filled in).  Host outputs: evals_host[m]
+ * ascending, resid_host[m], *iters.  Workspace: 9 D m doubles.
+ * HPHI_E_NUMERIC if the Rayleigh-Ritz basis has rank below m (a rank-deficient
+ * start block), HPHI_E_INVAL for D < 3 m. */
+HPHI_API int hphi_lobpcg(hphi_ctx *ctx, const hphi_ham *ham, int m, void *X, int max_iter, double tol,
+                         double *evals_host, double *resid_host, int *iters);
+
 /* ---- microcanonical TPQ step (Sec. 3.5.1) ---------------------------------------
  * Phi_{k+1} = U_m Phi_k, U_m = 1 - (dtau/2) H with dtau = 2 / (l n_sites): the
  * cTPQ step above with nmax = 1 (same arguments, layout and outputs).  The

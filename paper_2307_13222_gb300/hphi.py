@@ -107,6 +107,7 @@ _SIGS = {
     "hphi_lanczos": (i32, [vp, vp, C.POINTER(_LanczosOpts), vp, vp, vp, vp, C.POINTER(_LanczosResult)]),
     "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
     "hphi_mtpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_lobpcg": (i32, [vp, vp, i32, vp, i32, dbl, vp, vp, C.POINTER(i32)]),
     "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
     "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
     "hphi_apply_sz_sum": (i32, [vp, vp, i32, vp, i64, vp, i64, vp]),
@@ -619,6 +620,23 @@ def hphi_szz_spectrum(ham: Hamiltonian, basis: Basis, gs, qs, z, max_steps: int,
     r = hphi_shifted_krylov(ham, rhs, z, max_steps, tol, check_every)
     Dq = np.stack([r["G"][col[k]] + (r["G"][col[k] + 1] if two[k] else 0.0) for k in range(nq)])
     return -Dq.imag, Dq, r
+
+
+def hphi_lobpcg(ham: Hamiltonian, X, max_iter: int, tol: float):
+    """The m lowest eigenpairs (m = X.shape[1] <= 32) by LOBPCG; X (FP64 CUDA,
+    [D][m] contiguous) holds the start block and receives the Ritz vectors.
+    Returns a dict (evals, resid, iters, converged); NOTCONV is reported."""
+    ctx = ham.ctx
+    if not X.is_cuda or X.dtype.itemsize != 8 or X.is_complex() or X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous FP64 CUDA block [D][m]")
+    m = X.shape[1]
+    ev, rs, it = np.zeros(m), np.zeros(m), i32(0)
+    ctx._sync_stream()
+    st = ctx.lib.hphi_lobpcg(ctx.h, ham.h, m, C.c_void_p(X.data_ptr()), int(max_iter), float(tol), _np(ev), _np(rs),
+                             C.byref(it))
+    if st not in (HPHI_OK, -4):
+        ctx.check(st)
+    return dict(evals=ev, resid=rs, iters=it.value, converged=st == HPHI_OK, status=st)
 
 
 def hphi_mtpq_step(ham: Hamiltonian, V, l: float, n_sites: int, norm2: np.ndarray):
