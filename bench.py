@@ -257,6 +257,10 @@ def run_native(args):
     basis = hphi.Basis(ctx, "SPIN_HALF", 32, 16)
     ham = hphi.Hamiltonian(ctx, basis, cfg["terms"])
     dim = basis.dim
+    tuned = None
+    if not args.no_autotune:  # launch settings chosen by the library's autotuner (untimed set-up)
+        import torch as _t
+        tuned = ham.autotune(_t.float32 if args.dtype == "f32" else _t.float64, 1, reps=2)
     K, W = args.steps, args.warmup
     clocks = ClockSampler(local)
     clocks.start()
@@ -296,6 +300,7 @@ def run_native(args):
         "ms_per_step": main["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": "heisenberg_square_4x8_Sz0", "n_sites": 32, "dim": dim, "step": "lanczos_iteration",
+                   "launch": ham.get_tuning(), "autotuned_ms": tuned[0] if tuned else None,
                    "vectors": args.dtype, "scalars": "f64", "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (one vector = %.1f GB)" % (main["es"] * dim / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -561,6 +566,7 @@ def run_ctpq26(args):
     b = hphi.Basis(ctx, "SPIN_HALF_GC", 26)
     h = hphi.Hamiltonian(ctx, b, cfg["terms"])
     tdt = torch.complex64 if args.dtype == "f32" else torch.complex128
+    tuned = None if args.no_autotune else h.autotune(tdt, cfg["n_vec"], reps=2)
     V = torch.empty((b.dim, cfg["n_vec"]), dtype=tdt, device="cuda")
     hphi.hphi_random_vector(ctx, V, cfg["seed"])
     n2 = np.zeros(cfg["n_vec"])
@@ -600,6 +606,7 @@ def run_ctpq26(args):
                  ms / args.steps, args.dtype,
                  {"workload": "ctpq_rrg3_N26_B16", "dim": b.dim, "n_vec": cfg["n_vec"], "nmax": cfg["nmax"],
                   "dtau": cfg["dtau"], "vectors": "c64" if args.dtype == "f32" else "c128",
+                  "launch": h.get_tuning(), "autotuned_ms": tuned[0] if tuned else None,
                   "parallelism": f"replicas{world}",
                   "l2": "inputs larger than L2 (block = %.1f GB)" % (es * 16 * b.dim / 1e9)})
     line.update({"tpq_steps_per_s": world * args.steps / (ms * 1e-3), "roofline": roof,
@@ -816,6 +823,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the extra FP64 measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch settings")
     ap.add_argument("--lattice", default="6x5", help="apply workload: Lx x Ly of the square lattice")
     ap.add_argument("--variant", type=int, default=None, help="apply workload: H*x kernel variant (-1, 0, 1, 2)")
     ap.add_argument("--workload", choices=["square4x8"] + sorted(WORKLOADS), default="square4x8",

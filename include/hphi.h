@@ -176,6 +176,14 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  * Results do not depend on the knobs except through summation order of the
  * reductions (still deterministic for fixed knobs).  HPHI_E_INVAL for an
  * unknown knob or value. */
+/* hphi_ham_autotune: times every valid setting of the knobs below for
+ * hphi_apply_H on this Hamiltonian with nvec columns of dtype (reps timed
+ * launches each, after one warm-up; vectors allocated and freed here), keeps
+ * the fastest on the Hamiltonian and reports its time per launch (*best_ms)
+ * and the number of settings tried.  Later calls of any shape use the chosen
+ * settings.  HPHI_E_NOMEM if two vectors of that shape do not fit. */
+HPHI_API int hphi_ham_autotune(hphi_ctx *ctx, hphi_ham *ham, int dtype, int nvec, int reps, double *best_ms,
+                               int *n_tried);
 #define HPHI_TUNE_INNER_BITS 0
 #define HPHI_TUNE_SPLIT 1
 #define HPHI_TUNE_L2_HINTS 2

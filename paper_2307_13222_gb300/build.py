@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhphi.so")
 SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "vec.cu", "pattern.cu", "capi.cu", "drivers.cu",
            "spectrum.cu", "evolve.cu", "batch.cu", "serve.cu",
-           "lobpcg.cu"]
+           "lobpcg.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

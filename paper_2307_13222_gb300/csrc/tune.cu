@@ -1,0 +1,99 @@
+// Launch autotuner of the H*x kernels: times every valid setting of the
+// launch knobs (kernel variant, thread blocks per row block, L2 hints,
+// bond sharing of wide rows, form of the staged kernel) for one shape of
+// x (dtype, columns) on the Hamiltonian itself, and keeps the fastest.
+// The knobs change no result except the summation order of rows and
+// reductions.
+#include <float.h>
+
+#include <vector>
+
+#include "hphi_internal.cuh"
+
+using namespace hphi;
+
+extern "C" int hphi_ham_autotune(hphi_ctx *ctx, hphi_ham *ham, int dtype, int nvec, int reps, double *best_ms,
+                                 int *n_tried) {
+    if (!ctx || !ham) return HPHI_E_INVAL;
+    ctx->err.clear();
+    if (!valid_dtype(dtype)) return set_err(ctx, HPHI_E_INVAL, "unknown dtype %d", dtype);
+    const int cpl = is_complex(dtype) ? 2 : 1, nr = nvec * cpl;
+    if (nvec < 1 || nr > kMaxCols) return set_err(ctx, HPHI_E_INVAL, "1 <= real columns <= %d", kMaxCols);
+    if (reps < 1) reps = 3;
+    if (ham->device != ctx->device) return set_err(ctx, HPHI_E_INVAL, "hamiltonian belongs to another device");
+    HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t es = real_size(real_of(dtype)), bytes = (size_t)ham->D * nr * es;
+    void *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x);
+        return set_err(ctx, HPHI_E_NOMEM, "autotune vectors (2 x %zu bytes)", bytes);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved[6] = {ham->tune_variant, ham->tune_split, ham->tune_hints, ham->tune_coop, ham->tune_staged_lists,
+                          ham->tune_inner};
+    auto restore = [&](const int *v) {
+        ham->tune_variant = v[0];
+        ham->tune_split = v[1];
+        ham->tune_hints = v[2];
+        ham->tune_coop = v[3];
+        ham->tune_staged_lists = v[4];
+        ham->tune_inner = v[5];
+    };
+    auto cleanup = [&](int code) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(x);
+        cudaFree(y);
+        return code;
+    };
+    int st = hphi_random_vector(ctx, real_of(dtype), ham->D, nr, 1, x, nr);
+    if (st) return cleanup(st);
+    // candidate settings: variant x split x hints (x coop for 32-column rows, x form of the staged kernel)
+    std::vector<std::vector<int>> cand;
+    const bool spin = ham->model != HPHI_HUBBARD;
+    const std::vector<int> variants = spin ? std::vector<int>{0, 1, 2} : std::vector<int>{-1, 0};
+    for (int v : variants)
+        for (int sp : {1, 2, 4})
+            for (int hi : {0, 1}) {
+                if (v == 2 && sp != 1) continue;  // the staged kernel owns a row block per thread block
+                const std::vector<int> coops = (spin && nr == 32 && v == 1) ? std::vector<int>{0, 1} : std::vector<int>{-1};
+                const std::vector<int> forms = (v == 2) ? std::vector<int>{0, 1} : std::vector<int>{0};
+                for (int co : coops)
+                    for (int fo : forms) cand.push_back({v, sp, hi, co, fo, -1});
+            }
+    double best = DBL_MAX;
+    std::vector<int> best_v(saved, saved + 6);
+    int tried = 0;
+    for (const auto &c : cand) {
+        restore(c.data());
+        // warm-up; a setting the launcher rejects for this shape is skipped
+        int s2 = hphi_apply_H(ctx, ham, dtype, nvec, x, nvec, y, nvec, 1.0, 0.0);
+        if (s2) {
+            ctx->err.clear();
+            continue;
+        }
+        HPHI_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps && !s2; r++) s2 = hphi_apply_H(ctx, ham, dtype, nvec, x, nvec, y, nvec, 1.0, 0.0);
+        HPHI_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        HPHI_CUDA(ctx, cudaEventSynchronize(e1));
+        if (s2) {
+            ctx->err.clear();
+            continue;
+        }
+        float ms = 0.0f;
+        HPHI_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        tried++;
+        if (ms / reps < best) {
+            best = ms / reps;
+            best_v = c;
+        }
+    }
+    restore(best_v.data());
+    if (best_ms) *best_ms = best;
+    if (n_tried) *n_tried = tried;
+    return cleanup(tried > 0 ? HPHI_OK : set_err(ctx, HPHI_E_INVAL, "no launch setting applies to this shape"));
+}

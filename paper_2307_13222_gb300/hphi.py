@@ -97,6 +97,7 @@ _SIGS = {
     "hphi_ham_dim": (i64, [vp]),
     "hphi_ham_set_tuning": (i32, [vp, i32, i32]),
     "hphi_ham_get_tuning": (i32, [vp, i32, C.POINTER(i32)]),
+    "hphi_ham_autotune": (i32, [vp, vp, i32, i32, i32, C.POINTER(dbl), C.POINTER(i32)]),
     "hphi_apply_H": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, dbl, dbl]),
     "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
     "hphi_dot": (i32, [vp, i32, i64, i32, vp, i64, vp, i64, vp]),
@@ -282,6 +283,17 @@ class Hamiltonian:
         """Launch knobs of the H*x kernel: inner_bits, split, l2_hints, variant, coop, staged_lists."""
         for k, v in knobs.items():
             self.ctx.check(self.ctx.lib.hphi_ham_set_tuning(self.h, self.TUNE[k], int(v)))
+
+    def autotune(self, dtype, nvec: int = 1, reps: int = 3):
+        """Time every valid launch setting for nvec columns of dtype (a torch
+        dtype) and keep the fastest.  Returns (ms per launch, settings tried)."""
+        import torch
+        code = {torch.float64: F64, torch.float32: F32, torch.complex128: C128, torch.complex64: C64}[dtype]
+        ms, n = dbl(0.0), i32(0)
+        self.ctx._sync_stream()
+        self.ctx.check(self.ctx.lib.hphi_ham_autotune(self.ctx.h, self.h, code, int(nvec), int(reps), C.byref(ms),
+                                                      C.byref(n)))
+        return ms.value, n.value
 
     def get_tuning(self):
         out = {}

@@ -241,3 +241,18 @@ def test_staged_square_4x8_full_size_sampled(dtype, lists):
     rng = np.random.default_rng(18)
     rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
     assert _sampled_rows(m, h, dtype, 1, rows, 52) < (1e-15 if dtype == torch.float64 else 1e-6)
+
+
+@pytest.mark.parametrize("shape", ["sector", "full", "hubbard"])
+@pytest.mark.parametrize("dtype,nvec", [(torch.float32, 1), (torch.float64, 1), (torch.complex64, 16)])
+def test_autotune_keeps_results(shape, dtype, nvec):
+    if shape == "sector":
+        m, b, h = pair("SPIN_HALF", 16, 8, 0, heisenberg_terms(square(4, 4), 1.0))
+    elif shape == "full":
+        bonds = random_regular_graph(14, 3, 9)
+        m, b, h = pair("SPIN_HALF_GC", 14, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 3)))
+    else:
+        m, b, h = pair("HUBBARD", 8, 4, 3, hubbard_terms(8, chain(8), t=1.0, U=4.0, V=0.3))
+    ms, tried = h.autotune(dtype, nvec, reps=2)
+    assert ms > 0 and tried >= 2
+    _check(m, h, dtype, nvec, alpha=0.9, beta=0.0, seed=5)
