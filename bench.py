@@ -276,14 +276,15 @@ def run_native(args):
     hv_avg_ms = main["hv_ms"] / max(main["hv_launches"], 1)
     kern_bytes = 3.0 * main["es"] * dim
     achieved = kern_bytes / (hv_avg_ms * 1e-3) / 1e9
+    # DRAM bytes per launch of this kernel from the committed ncu summary (null if
+    # none exists for this dtype, or if the kernel is not the one captured there)
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"hv_traffic_{args.dtype}.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                traffic = json.load(f).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"hv_fused_square4x8_{args.dtype}_traffic.md")
+    if os.path.exists(tfile) and ham.get_tuning()["variant"] in (-1, 2) and args.dtype == "f32":
+        with open(tfile) as f:
+            for ln in f:
+                if ln.startswith("bytes_per_launch:"):
+                    traffic = float(ln.split(":")[1])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -777,15 +778,26 @@ def run_apply(args):
     import torch
     from paper_2307_13222_gb300 import hphi
     from workloads import square, heisenberg_terms
+    from workloads import random_regular_graph, uniform_couplings
     world, rank, local, dist, ctx = _setup(args)
-    Lx, Ly = (int(v) for v in args.lattice.lower().split("x"))
-    N = Lx * Ly
-    b = hphi.Basis(ctx, "SPIN_HALF", N, N // 2)
-    h = hphi.Hamiltonian(ctx, b, heisenberg_terms(square(Lx, Ly), 1.0))
+    if args.lattice.lower().startswith("rrg"):
+        # full space of a random 3-regular graph, 16 complex columns (the cTPQ block shape)
+        N = int(args.lattice[3:])
+        bonds = random_regular_graph(N, 3, 4)
+        b = hphi.Basis(ctx, "SPIN_HALF_GC", N)
+        h = hphi.Hamiltonian(ctx, b, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 1004)))
+        shape, ncol, Lx, Ly = (b.dim, 16), 32, N, 0
+        tdt = torch.complex64 if args.dtype == "f32" else torch.complex128
+    else:
+        Lx, Ly = (int(v) for v in args.lattice.lower().split("x"))
+        N = Lx * Ly
+        b = hphi.Basis(ctx, "SPIN_HALF", N, N // 2)
+        h = hphi.Hamiltonian(ctx, b, heisenberg_terms(square(Lx, Ly), 1.0))
+        shape, ncol = (b.dim,), 1
+        tdt = torch.float32 if args.dtype == "f32" else torch.float64
     if args.variant is not None:
         h.set_tuning(variant=args.variant)
-    tdt = torch.float32 if args.dtype == "f32" else torch.float64
-    x = torch.empty(b.dim, dtype=tdt, device="cuda")
+    x = torch.empty(shape, dtype=tdt, device="cuda")
     hphi.hphi_random_vector(ctx, x, 1)
     y = torch.empty_like(x)
     for _ in range(max(args.warmup, 1)):
@@ -800,12 +812,13 @@ def run_apply(args):
     e1.record()
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
-    es = 4 if tdt == torch.float32 else 8
+    es = (4 if args.dtype == "f32" else 8) * ncol
+    name = f"heisenberg_square_{Lx}x{Ly}_Sz0_apply" if Ly else f"heisenberg_rrg3_N{Lx}_block16c_apply"
     line = _base(args, world, "hv_gbps", job_gbps(world, args.steps * 2.0 * es * b.dim, ms), "GB/s", ms / args.steps,
-                 args.dtype, {"workload": f"heisenberg_square_{Lx}x{Ly}_Sz0_apply", "dim": b.dim,
+                 args.dtype, {"workload": name, "dim": b.dim, "columns": ncol,
                               "variant": h.get_tuning()["variant"], "parallelism": f"replicas{world}",
                               "l2": "vector of %.2f GB > L2" % (es * b.dim / 1e9)})
-    line.update({"roofline": _roofline(ctx, 2.0 * es * b.dim, "single-column H*x"), "gpu_launches": args.steps})
+    line.update({"roofline": _roofline(ctx, 2.0 * es * b.dim, "H*x (x + y)"), "gpu_launches": args.steps})
     return _finish(line, rank, dist, ctx)
 
 
@@ -824,7 +837,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch settings")
-    ap.add_argument("--lattice", default="6x5", help="apply workload: Lx x Ly of the square lattice")
+    ap.add_argument("--lattice", default="6x5",
+                    help="apply workload: Lx x Ly of the square lattice, or rrgN (full space, 16 complex columns)")
     ap.add_argument("--variant", type=int, default=None, help="apply workload: H*x kernel variant (-1, 0, 1, 2)")
     ap.add_argument("--workload", choices=["square4x8"] + sorted(WORKLOADS), default="square4x8",
                     help="square4x8 (default): Lanczos steps on the 4x8 sector; the others measure the "

@@ -166,10 +166,13 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         the row block's x in shared memory and low-half
  *                         ranks from shared tables (S^z sector, one column,
  *                         N_lo <= 16; automatic there for FP32 data)
- *   HPHI_TUNE_COOP        32-column rows: 1 = the lanes of a row split the
- *                         bond evaluation and share targets, 0 = every lane
- *                         evaluates every bond, -1 = 1 for FP32 and 0 for
- *                         FP64 data (default)
+ *   HPHI_TUNE_COOP        32-column rows: 1-5 = the lanes of a row split the
+ *                         bond evaluation and share targets (1: 8 targets per
+ *                         batch, registers for 2 thread blocks per SM; 2: 4
+ *                         targets, 3 blocks; 3: 4 targets, 4 blocks; 4: 4
+ *                         targets, 5 blocks; 5: 2 targets, 6 blocks), 0 =
+ *                         every lane evaluates every bond, -1 = 3 for FP32 and
+ *                         0 for FP64 data (default)
  *   HPHI_TUNE_STAGED_LISTS staged kernel: 1 = low-low targets and flipped
  *                         ranks from the per-low-half lists, 0 = from the
  *                         shared rank tables (default)

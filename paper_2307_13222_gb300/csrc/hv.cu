@@ -463,7 +463,7 @@ extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
         ham->tune_variant = value;
         return HPHI_OK;
     case HPHI_TUNE_COOP:
-        if (value < -1 || value > 1) return HPHI_E_INVAL;
+        if (value < -1 || value > 5) return HPHI_E_INVAL;
         ham->tune_coop = value;
         return HPHI_OK;
     case HPHI_TUNE_STAGED_LISTS:

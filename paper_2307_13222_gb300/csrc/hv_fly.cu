@@ -306,8 +306,10 @@ __global__ void __launch_bounds__(kThreads, (CPL == 1 && sizeof(T) == 4) ? 3 : 2
 // ones and broadcasts their targets by shuffle, then every lane gathers its
 // CPL columns of each target.  The bond work is done once per row instead of
 // once per lane.
-template <typename T, int CPL, int G, int RED>
-__global__ void __launch_bounds__(kThreads, 2) k_hvc(const HvArgs<T> a) {
+// KB: targets broadcast and gathered per batch; MINB: thread blocks per SM the
+// register budget is sized for (more resident warps, fewer loads in flight each).
+template <typename T, int CPL, int G, int RED, int KB, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_hvc(const HvArgs<T> a) {
     extern __shared__ double red_sm[];  // [nwarps][3][G*CPL]
     __shared__ HBlock<T> hb;
     __shared__ uint32_t ll_m[kMaxLLs];
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_hvc(const HvArgs<T> a) {
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
                 const unsigned gm = (bal >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u));
                 // broadcast the group's targets 8 at a time, then gather
-                constexpr int kB = G < 8 ? G : 8;
+                constexpr int kB = G < KB ? G : KB;
 #pragma unroll
                 for (int s0 = 0; s0 < G; s0 += kB) {
                     uint32_t ts[kB];
@@ -484,14 +486,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_hvc(const HvArgs<T> a) {
     }
 }
 
-template <typename T, int CPL, int G, int RED>
+template <typename T, int CPL, int G, int RED, int KB, int MINB>
 int go_c(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int *grid_out) {
     static int occ[64] = {0};
     const int dev = ctx->device;
     const size_t dyn = RED ? 3 * (kThreads / 32) * G * CPL * sizeof(double) : 0;
     if (occ[dev] == 0) {
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvc<T, CPL, G, RED>, kThreads, dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvc<T, CPL, G, RED, KB, MINB>, kThreads, dyn);
         occ[dev] = n > 0 ? n : 1;
     }
     const int split = a.P.split;
@@ -501,21 +503,33 @@ int go_c(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int *grid_out) 
     g *= split;
     *grid_out = (int)g;
     const int slot = prof_begin(ctx, PROF_HV);
-    k_hvc<T, CPL, G, RED><<<(int)g, kThreads, dyn, ctx->stream>>>(a);
+    k_hvc<T, CPL, G, RED, KB, MINB><<<(int)g, kThreads, dyn, ctx->stream>>>(a);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;
 }
 
-template <typename T, int CPL, int G>
+template <typename T, int CPL, int G, int KB, int MINB>
 int go_c_red(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid) {
     switch (red_mode) {
-    case 0: return go_c<T, CPL, G, 0>(ctx, ham, a, grid);
-    case 1: return go_c<T, CPL, G, 1>(ctx, ham, a, grid);
-    case 2: return go_c<T, CPL, G, 2>(ctx, ham, a, grid);
-    case 3: return go_c<T, CPL, G, 3>(ctx, ham, a, grid);
+    case 0: return go_c<T, CPL, G, 0, KB, MINB>(ctx, ham, a, grid);
+    case 1: return go_c<T, CPL, G, 1, KB, MINB>(ctx, ham, a, grid);
+    case 2: return go_c<T, CPL, G, 2, KB, MINB>(ctx, ham, a, grid);
+    case 3: return go_c<T, CPL, G, 3, KB, MINB>(ctx, ham, a, grid);
     default: return HPHI_E_INVAL;
     }
+}
+
+// bond sharing form: 1 = 8 targets per batch, 2 thread blocks per SM;
+// 2 = 4 targets, 3 blocks; 3 = 4 targets, 4 blocks; 4 = 4 targets, 5 blocks;
+// 5 = 2 targets, 6 blocks
+template <typename T, int CPL, int G>
+int go_coop(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int form, int red_mode, int *grid) {
+    if (form == 2) return go_c_red<T, CPL, G, 4, 3>(ctx, ham, a, red_mode, grid);
+    if (form == 3) return go_c_red<T, CPL, G, 4, 4>(ctx, ham, a, red_mode, grid);
+    if (form == 4) return go_c_red<T, CPL, G, 4, 5>(ctx, ham, a, red_mode, grid);
+    if (form == 5) return go_c_red<T, CPL, G, 2, 6>(ctx, ham, a, red_mode, grid);
+    return go_c_red<T, CPL, G, 8, 2>(ctx, ham, a, red_mode, grid);
 }
 
 template <typename T, int CPL, int G, int RED>
@@ -559,13 +573,14 @@ int launch_fly(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int G, in
     if (G == 1 && cpl == 1) return go_red<T, 1, 1>(ctx, ham, a, red_mode, grid);
     if (G == 1 && cpl == 2) return go_red<T, 2, 1>(ctx, ham, a, red_mode, grid);
     // 32-column rows: cooperative target generation unless the per-lane variant was asked for
-    // measured: shared bond work pays for FP32 rows, the per-lane form is faster for FP64
-    const bool coop = ham->tune_coop < 0 ? std::is_same<T, float>::value : ham->tune_coop != 0;
+    // measured: shared bond work with registers for 4 blocks per SM pays for FP32
+    // rows (-36 % on the N=26 block); the per-lane form is faster for FP64
+    const int coop = ham->tune_coop < 0 ? (std::is_same<T, float>::value ? 3 : 0) : ham->tune_coop;
     if constexpr (std::is_same<T, float>::value) {
-        if (G == 8 && cpl == 4) return coop ? go_c_red<T, 4, 8>(ctx, ham, a, red_mode, grid)
+        if (G == 8 && cpl == 4) return coop ? go_coop<T, 4, 8>(ctx, ham, a, coop, red_mode, grid)
                                             : go_red<T, 4, 8>(ctx, ham, a, red_mode, grid);
     } else {
-        if (G == 16 && cpl == 2) return coop ? go_c_red<T, 2, 16>(ctx, ham, a, red_mode, grid)
+        if (G == 16 && cpl == 2) return coop ? go_coop<T, 2, 16>(ctx, ham, a, coop, red_mode, grid)
                                              : go_red<T, 2, 16>(ctx, ham, a, red_mode, grid);
     }
     return HPHI_E_INVAL;

@@ -198,7 +198,7 @@ def test_kernel_variants_and_knobs(variant, split, hints, inner, shape, nvec):
         _check(m, h, dtype, nvec, alpha=0.9, beta=0.0 if nvec == 32 else 0.4, seed=nvec + split)
 
 
-@pytest.mark.parametrize("coop", [-1, 0, 1])
+@pytest.mark.parametrize("coop", [-1, 0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("split", [1, 3])
 @pytest.mark.parametrize("shape", ["sector", "full"])
 def test_wide_rows_cooperative_knob(coop, split, shape):

@@ -49,7 +49,7 @@ def test_tpq_sector_model():
     assert np.allclose(e, eo, rtol=1e-12) and np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)
 
 
-@pytest.mark.parametrize("coop", [-1, 0, 1])
+@pytest.mark.parametrize("coop", [-1, 0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_tpq_block_of_16_complex_vectors(coop, dtype):
     """16 complex vectors = 32-column rows, the fused <x,Hx>, |Hx|^2, |x|^2
@@ -86,3 +86,38 @@ def test_mtpq_steps_match_oracle(dtype):
         assert np.allclose(e, eo, rtol=tol, atol=tol) and np.allclose(logd, np.log(do), rtol=tol, atol=tol), step
         beta = hphi.mtpq_beta(step, l, N, e)
         assert np.allclose(beta, step * (2.0 / (l * N)) / (1.0 - eo / N / l), rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_ctpq_thermodynamics_small_member_of_the_benchmark_family(dtype):
+    """The benchmark's cTPQ run (16 complex vectors, nmax 6, dtau 0.02) on a
+    14-site member of its random 3-regular graph family for 1000 steps
+    (beta up to 20): E(T) and C(T) from the paper's bootstrap against the exact
+    canonical averages of the spectrum (dense, sector by sector)."""
+    import oracle as O
+    N = 14
+    bonds = random_regular_graph(N, 3, 4)
+    terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 1004))
+    m, b, h = pair("SPIN_HALF_GC", N, 0, 0, terms)
+    evals = np.concatenate([np.linalg.eigvalsh(O.dense_matrix(O.Model("SPIN_HALF", N, n, 0, terms)))
+                            for n in range(N + 1)])
+    nvec, steps, dtau = 16, 1000, 0.02
+    V = torch.from_numpy(random_vectors(m.dim, nvec, 4, complex_=True)).to(dtype).cuda().contiguous()
+    norm2 = np.zeros(nvec)
+    E = np.zeros((nvec, steps))
+    E2 = np.zeros((nvec, steps))
+    logn = np.zeros((nvec, steps))
+    acc = np.zeros(nvec)
+    for k in range(steps):
+        e, h2, logd = hphi.hphi_tpq_step(h, V, dtau, 6, norm2)
+        E[:, k], E2[:, k], logn[:, k] = e, h2, acc
+        acc = acc + logd
+    betas = dtau * np.arange(steps)
+    bs = O.bootstrap_tpq(E, E2, logn, P=nvec, M=nvec // 2, seed=1)
+    mean, sd = bs["H"]
+    fl, fsd = bs["fluct"]
+    for k in (50, 250, 500, 999):
+        ex, cx = O.canonical_thermo(evals, np.array([1.0 / betas[k]]))
+        assert abs(mean[k] - ex[0]) < 4 * sd[k] + 0.02 * abs(ex[0]), (k, mean[k], ex[0], sd[k])
+        c = betas[k] ** 2 * fl[k]
+        assert abs(c - cx[0]) < 4 * betas[k] ** 2 * fsd[k] + 0.1 * abs(cx[0]) + 0.02, (k, c, cx[0])
