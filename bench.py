@@ -573,6 +573,9 @@ def run_ctpq26(args):
     n2 = np.zeros(cfg["n_vec"])
     for _ in range(max(args.warmup, 1)):
         hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+    if args.curve:  # the run starts at beta = 0 from the seeded vectors
+        hphi.hphi_random_vector(ctx, V, cfg["seed"])
+        n2[:] = 0.0
     torch.cuda.synchronize()
     ctx.profile(True)
     ctx.profile_read(0)
@@ -580,14 +583,31 @@ def run_ctpq26(args):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    rec_e, rec_h2, rec_ln, acc = [], [], [], np.zeros(cfg["n_vec"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         e, h2, logd = hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+        if args.curve:
+            rec_e.append(e)
+            rec_h2.append(h2)
+            rec_ln.append(acc.copy())
+            acc = acc + logd
     e1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    curve = None
+    if args.curve:
+        # E(T) and C(T) per site from the paper's bootstrap (16 samples, 8 resamplings)
+        (hm, hs), (fm, fs) = hphi.tpq_thermo(np.array(rec_e).T, np.array(rec_h2).T, np.array(rec_ln).T, P=16, M=8)
+        betas = cfg["dtau"] * np.arange(args.steps)
+        curve = []
+        for T in (8.0, 4.0, 2.0, 1.0, 0.5, 0.25, 0.1, 0.05, 0.025):
+            k = int(round(1.0 / T / cfg["dtau"]))
+            if 0 < k < args.steps:
+                curve.append({"T": 1.0 / betas[k], "E_per_site": hm[k] / 26, "E_sd": hs[k] / 26,
+                              "C_per_site": betas[k] ** 2 * fm[k] / 26, "C_sd": betas[k] ** 2 * fs[k] / 26})
     es = 8 if tdt == torch.complex64 else 16
     # algorithmic bytes of one Horner stage: read V + gather W + write W' per complex column
     stage_bytes = 3.0 * es * cfg["n_vec"] * b.dim
@@ -610,6 +630,8 @@ def run_ctpq26(args):
                   "launch": h.get_tuning(), "autotuned_ms": tuned[0] if tuned else None,
                   "parallelism": f"replicas{world}",
                   "l2": "inputs larger than L2 (block = %.1f GB)" % (es * 16 * b.dim / 1e9)})
+    if curve is not None:
+        line["thermo"] = curve
     line.update({"tpq_steps_per_s": world * args.steps / (ms * 1e-3), "roofline": roof,
                  "gpu_launches": args.steps * (cfg["nmax"] + 2), "e_last": float(np.mean(e))})
     if ck:
@@ -837,6 +859,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch settings")
+    ap.add_argument("--curve", action="store_true",
+                    help="ctpq26: run from beta = 0 and report E(T), C(T) per site (bootstrap)")
     ap.add_argument("--lattice", default="6x5",
                     help="apply workload: Lx x Ly of the square lattice, or rrgN (full space, 16 complex columns)")
     ap.add_argument("--variant", type=int, default=None, help="apply workload: H*x kernel variant (-1, 0, 1, 2)")

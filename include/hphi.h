@@ -165,7 +165,7 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         one-thread-per-row kernel for Hubbard), 2 = staged:
  *                         the row block's x in shared memory and low-half
  *                         ranks from shared tables (S^z sector, one column,
- *                         N_lo <= 16; automatic there for FP32 data)
+ *                         N_lo <= 16; automatic there)
  *   HPHI_TUNE_COOP        32-column rows: 1-5 = the lanes of a row split the
  *                         bond evaluation and share targets (1: 8 targets per
  *                         batch, registers for 2 thread blocks per SM; 2: 4
@@ -173,9 +173,11 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         targets, 5 blocks; 5: 2 targets, 6 blocks), 0 =
  *                         every lane evaluates every bond, -1 = 3 for FP32 and
  *                         0 for FP64 data (default)
- *   HPHI_TUNE_STAGED_LISTS staged kernel: 1 = low-low targets and flipped
- *                         ranks from the per-low-half lists, 0 = from the
- *                         shared rank tables (default)
+ *   HPHI_TUNE_STAGED_LISTS staged kernel, two bits: bit 0 set = low-low
+ *                         targets and flipped ranks from the per-low-half
+ *                         lists, clear = from the shared rank tables; bit 1
+ *                         set = registers sized for one more thread block per
+ *                         SM; -1 = 3 for FP32 and 2 for FP64 data (default)
  * Results do not depend on the knobs except through summation order of the
  * reductions (still deterministic for fixed knobs).  HPHI_E_INVAL for an
  * unknown knob or value. */

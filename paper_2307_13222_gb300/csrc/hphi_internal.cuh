@@ -170,7 +170,7 @@ struct hphi_ham {
     int tune_hints = 1;
     int tune_variant = -1;       // -1: automatic, 1: on-the-fly ranks (spin), 0: table-driven
     int tune_coop = -1;          // wide rows: lanes of a row share the bond work (-1: FP32 only)
-    int tune_staged_lists = 0;   // staged kernel: 1 = neighbour lists, 0 = shared rank tables
+    int tune_staged_lists = -1;  // staged kernel: bit 0 lists, bit 1 one more block per SM (-1: by dtype)
 };
 
 namespace hphi {

@@ -72,8 +72,8 @@ __device__ __forceinline__ int binom8(int k) {  // C(8, k), 0 outside 0..8
 // TAB = 0: targets in the block from the shared rank tables (T1, T2_p); TAB = 1:
 // from the Hamiltonian's per-low-half lists (low-low targets and coefficient
 // indices, ranks of the low half with one bit flipped), read coalesced.
-template <typename T, int RED, int TAB>
-__global__ void __launch_bounds__(kStagedThreads, sizeof(T) == 4 ? 2 : 1) k_hvs(const HvArgs<T> a, uint32_t xs_len) {
+template <typename T, int RED, int TAB, int MINB>
+__global__ void __launch_bounds__(kStagedThreads, MINB) k_hvs(const HvArgs<T> a, uint32_t xs_len) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     T *xs = (T *)s_raw;
     double *red_sm = (double *)(s_raw + ((xs_len * sizeof(T) + 15) & ~(size_t)15));
@@ -234,16 +234,16 @@ __global__ void __launch_bounds__(kStagedThreads, sizeof(T) == 4 ? 2 : 1) k_hvs(
     }
 }
 
-template <typename T, int RED, int TAB>
+template <typename T, int RED, int TAB, int MINB>
 int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len, int *grid_out) {
     const size_t dyn = ((xs_len * sizeof(T) + 15) & ~(size_t)15) + 3 * (kStagedThreads / 32) * sizeof(double);
     static int occ[64] = {0};
     static size_t occ_dyn[64] = {0};
     const int dev = ctx->device;
     if (occ[dev] == 0 || occ_dyn[dev] != dyn) {
-        cudaFuncSetAttribute(k_hvs<T, RED, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaFuncSetAttribute(k_hvs<T, RED, TAB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvs<T, RED, TAB>, kStagedThreads, dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvs<T, RED, TAB, MINB>, kStagedThreads, dyn);
         occ[dev] = n;
         occ_dyn[dev] = dyn;
     }
@@ -253,7 +253,7 @@ int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
     if (g < 1) g = 1;
     *grid_out = (int)g;
     const int slot = prof_begin(ctx, PROF_HV);
-    k_hvs<T, RED, TAB><<<(int)g, kStagedThreads, dyn, ctx->stream>>>(a, xs_len);
+    k_hvs<T, RED, TAB, MINB><<<(int)g, kStagedThreads, dyn, ctx->stream>>>(a, xs_len);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;
@@ -270,13 +270,13 @@ uint32_t staged_block_len(const hphi_ham *ham) {
     return m;
 }
 
-template <typename T, int TAB>
+template <typename T, int TAB, int MINB>
 int staged_red(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xl, int red_mode, int *grid) {
     switch (red_mode) {
-    case 0: return go_s<T, 0, TAB>(ctx, ham, a, xl, grid);
-    case 1: return go_s<T, 1, TAB>(ctx, ham, a, xl, grid);
-    case 2: return go_s<T, 2, TAB>(ctx, ham, a, xl, grid);
-    case 3: return go_s<T, 3, TAB>(ctx, ham, a, xl, grid);
+    case 0: return go_s<T, 0, TAB, MINB>(ctx, ham, a, xl, grid);
+    case 1: return go_s<T, 1, TAB, MINB>(ctx, ham, a, xl, grid);
+    case 2: return go_s<T, 2, TAB, MINB>(ctx, ham, a, xl, grid);
+    case 3: return go_s<T, 3, TAB, MINB>(ctx, ham, a, xl, grid);
     default: return HPHI_E_INVAL;
     }
 }
@@ -284,9 +284,24 @@ int staged_red(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t 
 template <typename T>
 int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid) {
     const uint32_t xl = staged_block_len(ham);
-    // the list form needs the packed low-low lists
-    if (ham->tune_staged_lists && a.P.ll_pk) return staged_red<T, 1>(ctx, ham, a, xl, red_mode, grid);
-    return staged_red<T, 0>(ctx, ham, a, xl, red_mode, grid);
+    // tune_staged_lists: bit 0 = the list form (needs the packed low-low lists), bit 1 =
+    // registers sized for one more thread block per SM
+    // automatic form (measured on the 6x5 and 4x8 sectors): FP32 lists with registers for
+    // 3 blocks per SM (-23 %), FP64 rank tables with registers for 2 (-7 to -27 %)
+    const int form = ham->tune_staged_lists >= 0 ? ham->tune_staged_lists : (std::is_same<T, float>::value ? 3 : 2);
+    const bool lists = (form & 1) && a.P.ll_pk;
+    const bool more = (form & 2) != 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (more) return lists ? staged_red<T, 1, 3>(ctx, ham, a, xl, red_mode, grid)
+                               : staged_red<T, 0, 3>(ctx, ham, a, xl, red_mode, grid);
+        return lists ? staged_red<T, 1, 2>(ctx, ham, a, xl, red_mode, grid)
+                     : staged_red<T, 0, 2>(ctx, ham, a, xl, red_mode, grid);
+    } else {
+        if (more) return lists ? staged_red<T, 1, 2>(ctx, ham, a, xl, red_mode, grid)
+                               : staged_red<T, 0, 2>(ctx, ham, a, xl, red_mode, grid);
+        return lists ? staged_red<T, 1, 1>(ctx, ham, a, xl, red_mode, grid)
+                     : staged_red<T, 0, 1>(ctx, ham, a, xl, red_mode, grid);
+    }
 }
 
 template int launch_staged<float>(hphi_ctx *, const hphi_ham *, const HvArgs<float> &, int, int *);

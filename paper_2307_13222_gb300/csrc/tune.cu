@@ -62,7 +62,7 @@ extern "C" int hphi_ham_autotune(hphi_ctx *ctx, hphi_ham *ham, int dtype, int nv
                 if (v == 2 && sp != 1) continue;  // the staged kernel owns a row block per thread block
                 const std::vector<int> coops =
                     (spin && nr == 32 && v == 1) ? std::vector<int>{0, 1, 2, 3, 4, 5} : std::vector<int>{-1};
-                const std::vector<int> forms = (v == 2) ? std::vector<int>{0, 1} : std::vector<int>{0};
+                const std::vector<int> forms = (v == 2) ? std::vector<int>{0, 1, 2, 3} : std::vector<int>{0};
                 for (int co : coops)
                     for (int fo : forms) cand.push_back({v, sp, hi, co, fo, -1});
             }

@@ -664,6 +664,32 @@ def hphi_mtpq_step(ham: Hamiltonian, V, l: float, n_sites: int, norm2: np.ndarra
     return e, h2, logd
 
 
+def tpq_thermo(e, h2, log_norm, P: int, M: int, seed: int = 1):
+    """E(beta_k) and C(beta_k) / beta_k^2 of cTPQ samples by the bootstrap of
+    Sec. 3.5.1: M resamplings of P sample indices (drawn with replacement);
+    each resampling weights sample n at step k by its norm N_k^n relative to
+    sample 0's, <A>_m = sum_n w_n A_n / sum_n w_n; returns (mean, sd) of <H>
+    and of <H^2> - <H>^2 over the M resamplings, sd with 1/(M - 1).
+    Inputs [n_samples][n_steps]: <H>, <H^2> per sample and log N_k."""
+    e, h2, ln = (np.asarray(a, dtype=np.float64) for a in (e, h2, log_norm))
+    rng = np.random.default_rng(seed)
+    draws = rng.integers(0, e.shape[0], size=(M, P))
+    rel = np.exp(ln - ln[0:1, :])
+    hm = np.empty((M, e.shape[1]))
+    fm = np.empty((M, e.shape[1]))
+    for i in range(M):
+        w = rel[draws[i]]
+        z = w.sum(axis=0)
+        a1 = (w * e[draws[i]]).sum(axis=0) / z
+        a2 = (w * h2[draws[i]]).sum(axis=0) / z
+        hm[i], fm[i] = a1, a2 - a1 * a1
+
+    def msd(a):
+        mu = a.mean(axis=0)
+        return mu, (np.sqrt(((a - mu) ** 2).sum(axis=0) / (M - 1)) if M > 1 else np.zeros_like(mu))
+    return msd(hm), msd(fm)
+
+
 def mtpq_beta(k: int, l: float, n_sites: int, e) -> np.ndarray:
     """beta_k = k dtau / (1 - u_k / l), dtau = 2 / (l N_s), u_k = e / N_s (Sec. 3.5.1)."""
     dtau = 2.0 / (l * n_sites)

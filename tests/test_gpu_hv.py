@@ -219,7 +219,7 @@ def test_wide_rows_cooperative_knob(coop, split, shape):
 
 @pytest.mark.parametrize("N,nup", [(12, 6), (13, 4), (17, 8), (20, 7), (22, 11)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("lists", [0, 1])
+@pytest.mark.parametrize("lists", [0, 1, 2, 3])
 def test_staged_kernel(N, nup, dtype, lists):
     """Shared-memory staged kernel (spin sector, one column): low halves of
     4 to 11 bits, every popcount class, random XXZ couplings incl. zero Jxy."""
@@ -234,7 +234,7 @@ def test_staged_kernel(N, nup, dtype, lists):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("lists", [0, 1])
+@pytest.mark.parametrize("lists", [0, 1, 2, 3])
 def test_staged_square_4x8_full_size_sampled(dtype, lists):
     m, b, h = pair("SPIN_HALF", 32, 16, 0, heisenberg_terms(square(8, 4), 1.0))
     h.set_tuning(variant=2, staged_lists=lists)

@@ -140,3 +140,19 @@ def test_mtpq_temperature_follows_the_canonical_energy():
             for b_, u_ in zip(beta, u):
                 ec, _ = O.canonical_thermo(E, np.array([1.0 / b_]))
                 assert abs(u_ - ec[0] / N) < 0.05, (k, u_, ec[0] / N)
+
+
+def test_binding_bootstrap_agrees_with_the_oracle():
+    """The binding's post-processing of cTPQ samples (E, C/beta^2 by the
+    paper's bootstrap) against the oracle's, on random sample data."""
+    import numpy as np
+    import oracle as O
+    from paper_2307_13222_gb300.hphi import tpq_thermo
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=(12, 30))
+    h2 = e * e + rng.random(size=(12, 30))
+    ln = np.cumsum(rng.normal(scale=0.1, size=(12, 30)), axis=1)
+    (hm, hs), (fm, fs) = tpq_thermo(e, h2, ln, P=12, M=6, seed=5)
+    bs = O.bootstrap_tpq(e, h2, ln, P=12, M=6, seed=5)
+    assert np.allclose(hm, bs["H"][0], rtol=1e-12) and np.allclose(hs, bs["H"][1], rtol=1e-12)
+    assert np.allclose(fm, bs["fluct"][0], rtol=1e-12) and np.allclose(fs, bs["fluct"][1], rtol=1e-12)
