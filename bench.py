@@ -266,6 +266,7 @@ def run_native(args):
     clocks.start()
     main = measure_dtype(ctx, ham, dim, args.dtype, K, W, dist, world)
     ck = clocks.stop()
+    kernel_name = ctx.last_kernel()  # the fused H*x kernel of the timed Lanczos steps
     other = None
     if args.dtype == "f32" and not args.no_fp64:
         other = measure_dtype(ctx, ham, dim, "f64", max(2, K // 4), 1, dist, world)
@@ -276,15 +277,19 @@ def run_native(args):
     hv_avg_ms = main["hv_ms"] / max(main["hv_launches"], 1)
     kern_bytes = 3.0 * main["es"] * dim
     achieved = kern_bytes / (hv_avg_ms * 1e-3) / 1e9
-    # DRAM bytes per launch of this kernel from the committed ncu summary (null if
-    # none exists for this dtype, or if the kernel is not the one captured there)
+    # DRAM bytes per launch of this kernel from the committed ncu summary: null
+    # unless the summary names exactly the kernel instance that ran here
     traffic = None
     tfile = os.path.join(ROOT, "profiles", f"hv_fused_square4x8_{args.dtype}_traffic.md")
-    if os.path.exists(tfile) and ham.get_tuning()["variant"] in (-1, 2) and args.dtype == "f32":
+    if os.path.exists(tfile):
+        rec = {}
         with open(tfile) as f:
             for ln in f:
-                if ln.startswith("bytes_per_launch:"):
-                    traffic = float(ln.split(":")[1])
+                if ":" in ln and ln.split(":")[0] in ("kernel", "bytes_per_launch"):
+                    k, v = ln.split(":", 1)
+                    rec[k] = v.strip()
+        if rec.get("kernel") == kernel_name and "bytes_per_launch" in rec:
+            traffic = float(rec["bytes_per_launch"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -305,7 +310,7 @@ def run_native(args):
                    "vectors": args.dtype, "scalars": "f64", "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (one vector = %.1f GB)" % (main["es"] * dim / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_hv (fused Lanczos H*x)",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel_name,
                      "peak_kind": peak_kind, "avg_launch_ms": hv_avg_ms},
         "gpu_launches": gpu_launches,
         "kernel_ms": {"hv": main["hv_ms"], "vector": main["vec_ms"], "hv_launches": main["hv_launches"],

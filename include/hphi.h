@@ -103,6 +103,10 @@ HPHI_API int hphi_ctx_set_stream(hphi_ctx *ctx, void *stream);
 HPHI_API void hphi_ctx_destroy(hphi_ctx *ctx);
 /* Message of the last failing call on this context ("" if none). */
 HPHI_API const char *hphi_last_error(const hphi_ctx *ctx);
+/* Name of the last H*x kernel this context launched, with the template
+ * arguments that select its code path (e.g. "k_hvp<f32,512,RED1,MINB2>");
+ * "" before the first launch.  For matching profiles to launches. */
+HPHI_API const char *hphi_last_kernel(const hphi_ctx *ctx);
 /* Number of SMs of the context's device (grid sizing information). */
 HPHI_API int hphi_ctx_sm_count(const hphi_ctx *ctx);
 
@@ -165,7 +169,10 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         one-thread-per-row kernel for Hubbard), 2 = staged:
  *                         the row block's x in shared memory and low-half
  *                         ranks from shared tables (S^z sector, one column,
- *                         N_lo <= 16; automatic there)
+ *                         N_lo <= 16), 3 = bond-major: the staged block's H x
+ *                         accumulated in shared memory one bond at a time over
+ *                         precomputed lists of the rows the bond applies to
+ *                         (same shapes as 2; automatic there)
  *   HPHI_TUNE_COOP        32-column rows: 1-5 = the lanes of a row split the
  *                         bond evaluation and share targets (1: 8 targets per
  *                         batch, registers for 2 thread blocks per SM; 2: 4

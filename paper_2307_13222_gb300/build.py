@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhphi.so")
-SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "vec.cu", "pattern.cu", "capi.cu", "drivers.cu",
+SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "vec.cu", "pattern.cu", "capi.cu", "drivers.cu",
            "spectrum.cu", "evolve.cu", "batch.cu", "serve.cu",
            "lobpcg.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -193,6 +193,7 @@ extern "C" void hphi_ctx_destroy(hphi_ctx *ctx) {
 }
 
 extern "C" const char *hphi_last_error(const hphi_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+extern "C" const char *hphi_last_kernel(const hphi_ctx *ctx) { return ctx ? ctx->last_kernel : ""; }
 
 extern "C" int hphi_ctx_sm_count(const hphi_ctx *ctx) { return ctx ? ctx->sm_count : 0; }
 

@@ -139,6 +139,8 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->aup);
     cudaFree(h->ll_pk);
     cudaFree(h->ja16);
+    cudaFree(h->ph_ent);
+    cudaFree(h->ph_off);
     cudaFree(h->dterms_d);
     cudaFree(h->rowstate);
     delete h;
@@ -147,6 +149,66 @@ void free_ham(hphi_ham *h) {
 int grid_of(int64_t n) {
     int64_t g = (n + 255) / 256;
     return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g));
+}
+
+// Per-class bond lists of the bond-major H*x kernel (S^z sector, N_lo <= 16).
+// Low halves of popcount p, in ascending order, have class positions
+// q = 0 .. C(N_lo, p) - 1 (Lin's ja).  For every class p:
+//   low-low bond k = (i, j) with Jxy != 0: the q whose bits i, j differ, each
+//     with q' = position of l ^ (2^i | 2^j) (same class);
+//   low bit b of a mixed bond, need in {0, 1}: the q with bit b = need, each
+//     with r = position of l ^ 2^b (class p - 1 if need = 1, else p + 1).
+// Entries q | q' << 16 in ascending q.  Each group also gets the offsets of
+// the kPhRanges + 1 boundaries q_r = len * r / kPhRanges, so that the warp that
+// owns rows [q_r, q_r') of a block finds its entries without searching.
+int build_bond_lists(hphi_ctx *ctx, hphi_ham *H, const std::vector<LLBond> &ll, const std::vector<int> &lowbits) {
+    const int nlo = H->nlo, nll = (int)ll.size(), nlb = (int)lowbits.size();
+    std::vector<std::vector<uint32_t>> cls(nlo + 1);
+    std::vector<uint32_t> pos((size_t)1 << nlo);
+    for (uint32_t l = 0; l < (1u << nlo); l++) {
+        std::vector<uint32_t> &c = cls[__builtin_popcount(l)];
+        pos[l] = (uint32_t)c.size();
+        c.push_back(l);
+    }
+    std::vector<uint32_t> ent;
+    std::vector<int32_t> off;
+    auto close_group = [&](size_t start, uint32_t len) {
+        size_t i = start;
+        for (int r = 0; r <= kPhRanges; r++) {
+            const uint32_t qb = (uint32_t)(((uint64_t)len * r) / kPhRanges);
+            while (i < ent.size() && (ent[i] & 0xFFFFu) < qb) i++;
+            off.push_back((int32_t)i);
+        }
+    };
+    for (int p = 0; p <= nlo; p++) {
+        const std::vector<uint32_t> &c = cls[p];
+        for (int k = 0; k < nll; k++) {
+            const size_t start = ent.size();
+            const uint32_t m = (1u << ll[k].i) | (1u << ll[k].j);
+            if (ll[k].cxy != 0.0)
+                for (uint32_t q = 0; q < c.size(); q++) {
+                    const uint32_t lm = c[q] & m;
+                    if (lm != 0 && lm != m) ent.push_back(q | pos[c[q] ^ m] << 16);
+                }
+            close_group(start, (uint32_t)c.size());
+        }
+    }
+    H->ph_mx0 = (int64_t)off.size();
+    for (int p = 0; p <= nlo; p++) {
+        const std::vector<uint32_t> &c = cls[p];
+        for (int bi = 0; bi < nlb; bi++)
+            for (uint32_t need = 0; need < 2; need++) {
+                const size_t start = ent.size();
+                const int b = lowbits[bi];
+                for (uint32_t q = 0; q < c.size(); q++)
+                    if (((c[q] >> b) & 1u) == need) ent.push_back(q | pos[c[q] ^ (1u << b)] << 16);
+                close_group(start, (uint32_t)c.size());
+            }
+    }
+    if (ent.size() >= ((size_t)1 << 31)) return HPHI_OK;  // lists unavailable: the kernel is not offered
+    int st;
+    if ((st = to_dev(ctx, &H->ph_ent, ent)) || (st = to_dev(ctx, &H->ph_off, off))) return st;
+    return HPHI_OK;
 }
 
 int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) {
@@ -243,6 +305,7 @@ int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) 
     cudaFree(d_ll);
     cudaFree(d_lb);
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_spin_tables");
+    if (sector && nlo <= 16 && ll.size() <= 128) return build_bond_lists(ctx, H, ll, lowbits);
     return HPHI_OK;
 }
 

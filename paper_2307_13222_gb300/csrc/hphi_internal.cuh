@@ -37,6 +37,7 @@ constexpr int kMaxGroups = 4;   // byte groups of the low half (<= 32 bits)
 constexpr int kMaxCoef = 512;   // coefficient table (ELL coefficient indices)
 constexpr int kMaxBond = 256;   // bonds per class in the descriptor
 constexpr int kMaxCols = 128;   // real columns of one H*x launch
+constexpr int kPhRanges = 32;   // row ranges of a block in the bond-major kernel's list offsets
 constexpr int kThreads = 256;   // threads per block of the H*x kernel
 
 enum Model { kSpin = HPHI_SPIN_HALF, kSpinGC = HPHI_SPIN_HALF_GC, kHubbard = HPHI_HUBBARD };
@@ -108,6 +109,7 @@ struct hphi_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
+    char last_kernel[96] = {0};  // the last H*x kernel launched (name and template arguments)
     // reduction scratch: per-block partials and the reduced values
     double *partials = nullptr;
     size_t partials_n = 0;
@@ -158,6 +160,12 @@ struct hphi_ham {
     double *aup = nullptr;       // diagonal part of the up string alone
     uint32_t *ll_pk = nullptr;   // packed low-low lists (target | coefficient index << 24)
     uint16_t *ja16 = nullptr;    // Lin's ja as 16-bit ranks (spin sector, N_lo <= 16)
+    // per-class bond lists of the bond-major kernel (spin sector, N_lo <= 16):
+    // entries q | q' << 16 (class positions), grouped by (popcount p, bond),
+    // with offsets per group at kPhRanges + 1 row-range boundaries
+    uint32_t *ph_ent = nullptr;
+    int32_t *ph_off = nullptr;
+    int64_t ph_mx0 = 0;          // first offset row of the mixed-bond groups
     int max_row_entries = 0;
     // plain term list (host and device) and, for the S^z sector, the state of
     // every row (built on first use by the small-problem solver)
@@ -168,7 +176,7 @@ struct hphi_ham {
     int tune_inner = -1;
     int tune_split = 1;
     int tune_hints = 1;
-    int tune_variant = -1;       // -1: automatic, 1: on-the-fly ranks (spin), 0: table-driven
+    int tune_variant = -1;       // -1 automatic, 0 table-driven, 1 on-the-fly ranks, 2 staged, 3 bond-major
     int tune_coop = -1;          // wide rows: lanes of a row share the bond work (-1: FP32 only)
     int tune_staged_lists = -1;  // staged kernel: bit 0 lists, bit 1 one more block per SM (-1: by dtype)
 };

@@ -301,10 +301,9 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         const T *xs = (const T *)L.x + c0;
         T *ys = (T *)L.y + c0;
         const T *vs = L.v ? (const T *)L.v + c0 : nullptr;
-        // spin sector, one column: the staged kernel (variant 2)
-        // automatic (measured faster than the table-driven kernel on the 6x5 and 4x8 sectors,
-        // FP32 by 23-37 %, FP64 by 7-27 %)
-        const bool staged = (ham->tune_variant == 2 || ham->tune_variant < 0) &&
+        // spin sector, one column: the staged kernels (variants 2 and 3), automatic there
+        // (measured faster than the table-driven kernel on the 6x5 and 4x8 sectors)
+        const bool staged = (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
                             ham->model == HPHI_SPIN_HALF &&
                             ham->nlo <= 16 &&
                             ham->host.n_ll <= 128 && same_ld && red_mode >= 0 && L.ldx == 1 && L.ncol == 1 &&
@@ -375,15 +374,24 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         if (staged) {
             set_traversal(ctx, ham, a.P, (double)sizeof(T));
             a.P.split = 1;
-            st = launch_staged<T>(ctx, ham, a, red_mode, &grid);
+            // automatic: the bond-major kernel where its lists exist (measured 14-42 % faster than
+            // the staged kernel on the 6x5 and 4x8 sectors, FP32 and FP64)
+            const bool phased = ham->tune_variant == 3 || (ham->tune_variant < 0 && ham->ph_ent &&
+                                                           ham->host.n_ll <= 128);
+            st = phased ? launch_phased<T>(ctx, ham, a, red_mode, &grid)
+                        : launch_staged<T>(ctx, ham, a, red_mode, &grid);
         } else if (fG) {
             set_traversal(ctx, ham, a.P, (double)nc * sizeof(T) < 4.0 ? 4.0 : (double)nc * sizeof(T));
             a.P.split = ham->tune_split;
             st = launch_fly<T>(ctx, ham, a, fG, fcpl, red_mode, &grid);
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvo/k_hvc<%s,G%d,CPL%d,RED%d,coop%d>", tname<T>(),
+                     fG, fcpl, red_mode, ham->tune_coop);
         } else if (cpl) {
             set_traversal(ctx, ham, a.P, (double)cpl * sizeof(T) < 4.0 ? 4.0 : (double)cpl * sizeof(T));
             a.P.split = ham->tune_split;
             st = launch_lean<T>(ctx, ham, a, cpl, ldc, red_mode, &grid);
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvl<%s,CPL%d,LDC%d,RED%d>", tname<T>(), cpl, ldc,
+                     red_mode);
         } else {
             bool pair_ok = nc == 2 && (L.ldx % 2 == 0) && (L.ldy % 2 == 0) && (!L.v || L.ldv % 2 == 0) &&
                            aligned(xs, 2 * sizeof(T)) && aligned(ys, 2 * sizeof(T)) && aligned(vs, 2 * sizeof(T));
@@ -392,6 +400,7 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
                            (!L.v || (L.ldv * sizeof(T)) % vb == 0) && aligned(xs, vb) && aligned(ys, vb) &&
                            aligned(vs, vb);
             st = dispatch<T>(ctx, ham, a, pair_ok, quad_ok, &grid);
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hv<%s,NC%d>", tname<T>(), nc);
         }
         if (st) return st;
         L.sgrid[L.nslice] = grid;
@@ -459,7 +468,7 @@ extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
         ham->tune_hints = value;
         return HPHI_OK;
     case HPHI_TUNE_VARIANT:
-        if (value < -1 || value > 2) return HPHI_E_INVAL;
+        if (value < -1 || value > 3) return HPHI_E_INVAL;
         ham->tune_variant = value;
         return HPHI_OK;
     case HPHI_TUNE_COOP:

@@ -1,0 +1,238 @@
+// Bond-major H*x kernel for the spin-1/2 S^z sector with one column.
+//
+// Like the staged kernel, the thread block that owns row block h (the states
+// with high half h: rows base .. base + len - 1, low halves of popcount p)
+// first copies the block's slice of x into shared memory.  It then builds
+// (H x) of the block in a second shared array, one bond at a time:
+//   1. the diagonal and the high-high bonds, row by row (their targets sit at
+//      the same row offset in block h ^ m: coalesced loads);
+//   2. each low-low bond k = (i, j): acc[q] += c_k xs[q'] over the list of the
+//      rows of class p whose bits i and j differ, q' = Lin's rank of the
+//      flipped low half (same class, so the target is in shared memory);
+//   3. each mixed bond (a, b): acc[q] += c x[jb(h ^ 2^a) + r] over the list of
+//      the rows whose bit b equals 1 - h_a, r = rank of l ^ 2^b in class p -+ 1
+//      (ascending in q, so a warp's loads walk the target block in order);
+//   4. the epilogue y = alpha acc + beta y + gamma v with the fused reductions.
+// The lists hold only applicable (row, target) pairs, built once per
+// Hamiltonian on the host: no lane tests a bond, and none idles on a bond that
+// does not apply to its row.  Within one phase each row occurs at most once.
+// Warp w owns a fixed range of the block's rows in every phase (the lists
+// carry offsets at the range boundaries), so consecutive phases are ordered by
+// __syncwarp() alone.  Every row sums its terms in a fixed order, so results
+// are deterministic.  (Sec. 3.1.1 and Sec. 5: the spin-1/2 exchange terms and
+// their action on the bit-encoded basis.)
+#include "hvcommon.cuh"
+
+namespace hphi {
+
+namespace {
+
+constexpr int kPhUnroll = 4;   // list entries in flight per lane
+constexpr int kPhGathers = 4;  // high-high gathers in flight per row
+constexpr int kPhMaxLL = 128;
+
+template <typename T, int NT, int RED, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs_len) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T *xs = (T *)s_raw;
+    T *acs = xs + xs_len;
+    double *red_sm = (double *)(s_raw + ((2 * (size_t)xs_len * sizeof(T) + 15) & ~(size_t)15));
+    __shared__ HBlock<T> hb;
+    __shared__ T ll_c[kPhMaxLL];
+    const HvTables &P = a.P;
+    const HamDesc &D = *P.desc;
+    const int nll = D.n_ll;
+    for (int i = threadIdx.x; i < nll; i += NT) ll_c[i] = (T)D.ll[i].cxy;
+    const uint64_t keep = spol(P.hints, 0), stream = spol(P.hints, 1);
+    const T al = (T)(a.alpha_dev ? a.alpha_dev[0] : a.alpha[0]);
+    const T ga = (T)(a.gamma_dev ? a.gamma_dev[0] : a.gamma[0]);
+    const T be = (T)a.beta;
+    const bool use_beta = a.beta != 0.0, use_v = a.v != nullptr;
+    constexpr int NR = RED == 2 ? 3 : (RED ? 1 : 0);
+    RedAcc<T> racc[NR > 0 ? NR : 1];
+    constexpr int W = NT / 32, RPW = kPhRanges / W;
+    static_assert(kPhRanges % W == 0, "row ranges must split evenly over the warps");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *__restrict__ dlow = (const T *)P.dlow;
+    const T *__restrict__ X = a.x;
+    const uint32_t ld = (uint32_t)a.ldx;
+    const uint32_t *__restrict__ ent = P.ph_ent;
+    constexpr int OS = kPhRanges + 1;  // offsets per list group
+
+    for (int64_t c = blockIdx.x; c < P.nh; c += gridDim.x) {
+        const int64_t h = block_of(P, c);
+        __syncthreads();  // the previous block is done with hb, xs and acs
+        setup_block<T>(P, h, hb);
+        if (!hb.valid) continue;
+        const uint32_t base = (uint32_t)hb.base, len = hb.len, cp0 = hb.cp0;
+        const int p = P.n - __popcll((unsigned long long)h);
+        for (uint32_t q = threadIdx.x; q < len; q += NT) xs[q] = gload<T>(X + (base + q) * ld, keep);
+        __syncthreads();
+        const uint32_t q0 = (uint32_t)(((uint64_t)len * (uint32_t)(warp * RPW)) / kPhRanges);
+        const uint32_t q1 = (uint32_t)(((uint64_t)len * (uint32_t)((warp + 1) * RPW)) / kPhRanges);
+        // 1. diagonal and high-high bonds
+        const int nhh = hb.nhh;
+        for (uint32_t q = q0 + lane; q < q1; q += 32) {
+            const uint32_t cp = cp0 + q;
+            const uint32_t l = __ldg(P.lstate + cp);
+            T d = __ldg(dlow + cp) + hb.dh;
+            for (int g = 0; g < P.ngroups; g++) d += hb.tab[g][(l >> (8 * g)) & 255u];
+            T acc = d * xs[q];
+            const uint32_t row = base + q;
+            for (int k0 = 0; k0 < nhh; k0 += kPhGathers) {
+                T v[kPhGathers];
+#pragma unroll
+                for (int u = 0; u < kPhGathers; u++) {
+                    const int k = k0 + u;
+                    if (k < nhh)
+                        v[u] = gload<T>(X + (row + (uint32_t)hb.hh_delta[k]) * ld, hb.hh_outer[k] ? stream : keep);
+                }
+#pragma unroll
+                for (int u = 0; u < kPhGathers; u++)
+                    if (k0 + u < nhh) acc = fma(hb.hh_coef[k0 + u], v[u], acc);
+            }
+            acs[q] = acc;
+        }
+        __syncwarp();
+        // 2. low-low bonds, targets in shared memory
+        const int32_t *o = P.ph_off + (int64_t)p * nll * OS + warp * RPW;
+        for (int k = 0; k < nll; k++, o += OS) {
+            const int32_t s0 = __ldg(o), s1 = __ldg(o + RPW);
+            if (s0 == s1) continue;
+            const T ck = ll_c[k];
+            for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
+                uint32_t pk[kPhUnroll];
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++) {
+                    const int32_t i = i0 + 32 * u;
+                    pk[u] = i < s1 ? __ldg(ent + i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++)
+                    if (i0 + 32 * u < s1) {
+                        const uint32_t q = pk[u] & 0xFFFFu;
+                        acs[q] = fma(ck, xs[pk[u] >> 16], acs[q]);
+                    }
+            }
+            __syncwarp();
+        }
+        // 3. mixed bonds, targets in block h ^ 2^a
+        const int nlh = hb.nlh;
+        const int32_t *om = P.ph_off + P.ph_mx0 + warp * RPW;
+        for (int k = 0; k < nlh; k++) {
+            const int g = (p * P.ph_nlb + hb.lh_bi[k]) * 2 + hb.lh_need[k];
+            const int32_t s0 = __ldg(om + (int64_t)g * OS), s1 = __ldg(om + (int64_t)g * OS + RPW);
+            // a non-empty list implies a valid target block
+            if (s0 == s1 || hb.lh_base[k] < 0) continue;
+            const T cf = hb.lh_coef[k];
+            const uint32_t b2 = (uint32_t)hb.lh_base[k];
+            const uint64_t pol = hb.lh_outer[k] ? stream : keep;
+            for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
+                uint32_t pk[kPhUnroll];
+                T v[kPhUnroll];
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++) {
+                    const int32_t i = i0 + 32 * u;
+                    pk[u] = i < s1 ? __ldg(ent + i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++)
+                    if (i0 + 32 * u < s1) v[u] = gload<T>(X + (b2 + (pk[u] >> 16)) * ld, pol);
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++)
+                    if (i0 + 32 * u < s1) {
+                        const uint32_t q = pk[u] & 0xFFFFu;
+                        acs[q] = fma(cf, v[u], acs[q]);
+                    }
+            }
+            __syncwarp();
+        }
+        // 4. epilogue over the warp's rows
+        for (uint32_t q = q0 + lane; q < q1; q += 32) {
+            const T acc = acs[q];
+            const T xo = xs[q];
+            const uint32_t row = base + q;
+            T out = al * acc;
+            T *yr = a.y + row * ld;
+            if (use_beta) out = fma(be, cload<T>(yr, stream), out);
+            if (use_v) out = fma(ga, cload<T>(a.v + row * ld, stream), out);
+            cstore<T>(yr, stream, out);
+            if constexpr (RED == 1) racc[0].add(xo, out);
+            if constexpr (RED == 2) {
+                racc[0].add(xo, acc);
+                racc[1].add(acc, acc);
+                racc[2].add(xo, xo);
+            }
+            if constexpr (RED == 3) racc[0].add(out, out);
+        }
+    }
+    if constexpr (RED != 0) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            double val = racc[r].value();
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+            if (lane == 0) red_sm[warp * 3 + r] = val;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int r = threadIdx.x;
+            double s = 0.0;
+            if (r < NR)
+                for (int w = 0; w < W; w++) s += red_sm[w * 3 + r];
+            a.partials[((int64_t)blockIdx.x * 3 + r) * a.ncol] = s;
+        }
+    }
+}
+
+template <typename T, int NT, int RED, int MINB>
+int go_p(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len, int *grid_out) {
+    const size_t dyn = ((2 * (size_t)xs_len * sizeof(T) + 15) & ~(size_t)15) + 3 * (NT / 32) * sizeof(double);
+    static int occ[64] = {0};
+    static size_t occ_dyn[64] = {0};
+    const int dev = ctx->device;
+    if (occ[dev] == 0 || occ_dyn[dev] != dyn) {
+        cudaFuncSetAttribute(k_hvp<T, NT, RED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvp<T, NT, RED, MINB>, NT, dyn);
+        occ[dev] = n;
+        occ_dyn[dev] = dyn;
+    }
+    if (occ[dev] < 1) return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: a row block does not fit in shared memory");
+    int64_t g = (int64_t)occ[dev] * ctx->sm_count;
+    if (g > ham->nh) g = ham->nh;
+    if (g < 1) g = 1;
+    *grid_out = (int)g;
+    const int slot = prof_begin(ctx, PROF_HV);
+    k_hvp<T, NT, RED, MINB><<<(int)g, NT, dyn, ctx->stream>>>(a, xs_len);
+    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvp<%s,%d,RED%d,MINB%d>", tname<T>(), NT, RED, MINB);
+    prof_end(ctx, slot);
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+}  // namespace
+
+// FP32: 512 threads with registers for two blocks per SM (x and the
+// accumulator of a 12,870-row block take 103 KB of shared memory); FP64: one
+// block of 1024 threads (206 KB).
+template <typename T>
+int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid) {
+    if (!a.P.ph_ent || ham->host.n_ll > kPhMaxLL)
+        return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: no bond lists for this Hamiltonian");
+    const uint32_t xl = staged_block_len(ham);
+    constexpr bool F = std::is_same<T, float>::value;
+    constexpr int NT = F ? 512 : 1024, MB = F ? 2 : 1;
+    switch (red_mode) {
+    case 0: return go_p<T, NT, 0, MB>(ctx, ham, a, xl, grid);
+    case 1: return go_p<T, NT, 1, MB>(ctx, ham, a, xl, grid);
+    case 2: return go_p<T, NT, 2, MB>(ctx, ham, a, xl, grid);
+    case 3: return go_p<T, NT, 3, MB>(ctx, ham, a, xl, grid);
+    default: return HPHI_E_INVAL;
+    }
+}
+
+template int launch_phased<float>(hphi_ctx *, const hphi_ham *, const HvArgs<float> &, int, int *);
+template int launch_phased<double>(hphi_ctx *, const hphi_ham *, const HvArgs<double> &, int, int *);
+
+}  // namespace hphi

@@ -26,42 +26,6 @@ constexpr int kMaxLLs = 128;
 constexpr int kT2Rows = 17;  // popcounts 0..16 of a low half of <= 16 bits
 constexpr int kGathers = 4;  // global gathers in flight per chunk
 
-__device__ __forceinline__ uint64_t spol(int hints, int kind) {
-    uint64_t p;
-    if (!hints) asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-    else if (kind) asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    else asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-template <typename T>
-__device__ __forceinline__ T gload(const T *p, uint64_t pol) {
-    T v;
-    if constexpr (std::is_same<T, float>::value)
-        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-    else
-        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T cload(const T *p, uint64_t pol) {  // coherent (v may alias y)
-    T v;
-    if constexpr (std::is_same<T, float>::value)
-        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol) : "memory");
-    else
-        asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol) : "memory");
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ void cstore(T *p, uint64_t pol, T v) {
-    if constexpr (std::is_same<T, float>::value)
-        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-    else
-        asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
-}
-
 __device__ __forceinline__ int binom8(int k) {  // C(8, k), 0 outside 0..8
     constexpr int c[9] = {1, 8, 28, 56, 70, 56, 28, 8, 1};
     return (k < 0 || k > 8) ? 0 : c[k];
@@ -254,6 +218,7 @@ int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
     *grid_out = (int)g;
     const int slot = prof_begin(ctx, PROF_HV);
     k_hvs<T, RED, TAB, MINB><<<(int)g, kStagedThreads, dyn, ctx->stream>>>(a, xs_len);
+    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvs<%s,RED%d,TAB%d,MINB%d>", tname<T>(), RED, TAB, MINB);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;

@@ -35,6 +35,47 @@ struct RedAcc<float> {
     __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
 };
 
+// L2 cache policies and hinted loads / stores of the staged kernels: the
+// vector x is kept (evict_last), streamed rows are evicted first.
+__device__ __forceinline__ uint64_t spol(int hints, int kind) {
+    uint64_t p;
+    if (!hints) asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    else if (kind) asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+template <typename T>
+__device__ __forceinline__ T gload(const T *p, uint64_t pol) {
+    T v;
+    if constexpr (std::is_same<T, float>::value)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T cload(const T *p, uint64_t pol) {  // coherent (v may alias y)
+    T v;
+    if constexpr (std::is_same<T, float>::value)
+        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol) : "memory");
+    else
+        asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void cstore(T *p, uint64_t pol, T v) {
+    if constexpr (std::is_same<T, float>::value)
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+    else
+        asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
+template <typename T>
+inline const char *tname() { return std::is_same<T, float>::value ? "f32" : "f64"; }
+
 template <typename T>
 struct HvArgs {
     HvTables P;
@@ -87,6 +128,10 @@ inline HvTables make_tables(const hphi_ham *ham, int real_dtype) {
     P.split = 1;
     P.hints = ham->tune_hints;
     P.ja16 = ham->ja16;
+    P.ph_ent = ham->ph_ent;
+    P.ph_off = ham->ph_off;
+    P.ph_mx0 = ham->ph_mx0;
+    P.ph_nlb = ham->nlb;
     return P;
 }
 
@@ -142,5 +187,8 @@ int launch_fly(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int G, in
 // staged kernel (hv_staged.cu): spin sector, one column, N_lo <= 16
 template <typename T>
 int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
+template <typename T>
+int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
+uint32_t staged_block_len(const hphi_ham *ham);
 
 }  // namespace hphi

@@ -49,6 +49,10 @@ struct HvTables {
     int split;   // thread blocks sharing one row block
     int hints;   // L2 eviction-priority hints on
     const uint16_t *ja16;  // Lin's ja (16-bit), spin sector
+    const uint32_t *ph_ent;  // bond-major kernel: per-class bond lists, null if unavailable
+    const int32_t *ph_off;
+    int64_t ph_mx0;
+    int ph_nlb;              // low bits of the mixed bonds (list groups per class: 2 ph_nlb)
 };
 
 // Row block visited at traversal position c.

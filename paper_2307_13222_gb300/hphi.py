@@ -82,6 +82,7 @@ _SIGS = {
     "hphi_ctx_set_stream": (i32, [vp, vp]),
     "hphi_ctx_destroy": (None, [vp]),
     "hphi_last_error": (C.c_char_p, [vp]),
+    "hphi_last_kernel": (C.c_char_p, [vp]),
     "hphi_ctx_sm_count": (i32, [vp]),
     "hphi_ctx_profile": (i32, [vp, i32]),
     "hphi_ctx_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(dbl)]),
@@ -198,6 +199,10 @@ class Context:
     @property
     def sm_count(self) -> int:
         return int(self.lib.hphi_ctx_sm_count(self.h))
+
+    def last_kernel(self) -> str:
+        """Name and selecting template arguments of the last H*x kernel launched."""
+        return (self.lib.hphi_last_kernel(self.h) or b"").decode()
 
     def profile(self, enable: bool = True):
         """Record CUDA-event times around every kernel launch of this context."""

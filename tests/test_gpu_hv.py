@@ -243,6 +243,32 @@ def test_staged_square_4x8_full_size_sampled(dtype, lists):
     assert _sampled_rows(m, h, dtype, 1, rows, 52) < (1e-15 if dtype == torch.float64 else 1e-6)
 
 
+@pytest.mark.parametrize("N,nup", [(2, 1), (12, 6), (13, 4), (17, 8), (20, 7), (22, 11), (24, 12)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_bond_major_kernel(N, nup, dtype):
+    """Bond-major kernel (spin sector, one column): every popcount class, low
+    halves of 1 to 12 bits, random XXZ couplings incl. zero Jxy, so lists of
+    every length from empty up; with and without the accumulate term."""
+    rng = random.Random(N * 37 + nup)
+    pairs = list(itertools.combinations(range(N), 2))
+    pairs = rng.sample(pairs, min(len(pairs), 3 * N))
+    terms = [("XXZ", i, j, 0, rng.uniform(-1, 2), rng.uniform(-1, 2) if k % 7 else 0.0)
+             for k, (i, j) in enumerate(pairs)]
+    m, b, h = pair("SPIN_HALF", N, nup, 0, terms)
+    h.set_tuning(variant=3)
+    _check(m, h, dtype, 1, alpha=0.8, beta=0.0, seed=N)
+    _check(m, h, dtype, 1, alpha=-1.1, beta=0.35, seed=N + 1)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_bond_major_square_4x8_full_size_sampled(dtype):
+    m, b, h = pair("SPIN_HALF", 32, 16, 0, heisenberg_terms(square(8, 4), 1.0))
+    h.set_tuning(variant=3)
+    rng = np.random.default_rng(19)
+    rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
+    assert _sampled_rows(m, h, dtype, 1, rows, 53) < (1e-15 if dtype == torch.float64 else 1e-6)
+
+
 @pytest.mark.parametrize("shape", ["sector", "full", "hubbard"])
 @pytest.mark.parametrize("dtype,nvec", [(torch.float32, 1), (torch.float64, 1), (torch.complex64, 16)])
 def test_autotune_keeps_results(shape, dtype, nvec):

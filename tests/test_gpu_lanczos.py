@@ -119,7 +119,7 @@ def test_reorth_storage_beyond_device_memory_is_nomem():
     assert ei.value.code == -2
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 3])
 def test_chain16_each_single_column_kernel(variant):
     """The fused Lanczos step (reductions <x,y> and |y|^2 of the ground-state
     pass) through the table-driven and the staged kernels."""
