@@ -213,6 +213,21 @@ HPHI_API int hphi_ham_get_tuning(const hphi_ham *ham, int knob, int *value);
 HPHI_API int hphi_apply_H(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, const void *x, int64_t ldx, void *y,
                  int64_t ldy, double alpha, double beta);
 
+/* ---- H*x on host vectors (streaming) -------------------------------------
+ * y_b <- alpha * H x_b for nbatch independent vectors held in HOST memory:
+ * x_host and y_host each hold nbatch arrays of [D][nvec] elements of dtype,
+ * one after another (leading dimension nvec).  The library copies x_b to the
+ * device, applies H (the same kernels as hphi_apply_H) and copies y_b back;
+ * the copy of x_{b+1} to the device and of y_{b-1} to the host overlap the
+ * product of b (two device buffers each for x and y, context-owned, 4 * D *
+ * nvec * size bytes, grown on first use).  Pinned host memory (cudaHostAlloc,
+ * cudaHostRegister) gives full copy speed; pageable memory works with
+ * serialised copies.  Synchronous: returns once every y_b is on the host.
+ * x and y must not overlap.  Errors as hphi_apply_H, and HPHI_E_CUDA when
+ * the device buffers cannot be allocated. */
+HPHI_API int hphi_apply_H_host(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, int64_t nbatch,
+                               const void *x_host, void *y_host, double alpha);
+
 /* ---- matrix pattern (debug; the paper's Matrix Market export, Sec. 3.1.2) --
  * Rows [row0, row1) of H: for each row the distinct columns (ascending) with
  * the summed matrix element, the diagonal always included.  rowptr_host has

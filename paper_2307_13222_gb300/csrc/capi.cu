@@ -182,6 +182,14 @@ extern "C" void hphi_ctx_destroy(hphi_ctx *ctx) {
     cudaFree(ctx->dscal);
     cudaFreeHost(ctx->hscal);
     for (int i = 0; i < 4; i++) cudaFree(ctx->vec[i]);
+    for (int i = 0; i < 4; i++) cudaFree(ctx->io[i]);
+    for (int i = 0; i < 2; i++)
+        if (ctx->io_stream[i]) {
+            cudaStreamSynchronize(ctx->io_stream[i]);
+            cudaStreamDestroy(ctx->io_stream[i]);
+        }
+    for (auto e : ctx->io_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(ctx->dflag);
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
@@ -244,6 +252,89 @@ extern "C" int hphi_apply_H(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int n
     L.alpha_s = alpha;
     L.gamma_s = 0.0;
     return launch_hv(ctx, ham, L);
+}
+
+namespace {
+
+// Device buffers, copy streams and events of hphi_apply_H_host, made on first use.
+int ensure_io(hphi_ctx *ctx, size_t bytes) {
+    for (int i = 0; i < 2; i++)
+        if (!ctx->io_stream[i]) HPHI_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->io_stream[i], cudaStreamNonBlocking));
+    for (auto &e : ctx->io_ev)
+        if (!e) HPHI_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (ctx->io_bytes >= bytes) return HPHI_OK;
+    HPHI_CUDA(ctx, cudaDeviceSynchronize());
+    for (int i = 0; i < 4; i++) {
+        cudaFree(ctx->io[i]);
+        ctx->io[i] = nullptr;
+    }
+    ctx->io_bytes = 0;
+    for (int i = 0; i < 4; i++) {
+        cudaError_t e = cudaMalloc(&ctx->io[i], bytes);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < i; k++) {
+                cudaFree(ctx->io[k]);
+                ctx->io[k] = nullptr;
+            }
+            return cuda_err(ctx, e, "host-vector buffers");
+        }
+    }
+    ctx->io_bytes = bytes;
+    return HPHI_OK;
+}
+
+}  // namespace
+
+extern "C" int hphi_apply_H_host(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, int64_t nbatch,
+                                 const void *x_host, void *y_host, double alpha) {
+    if (!ctx || !ham) return HPHI_E_INVAL;
+    ctx->err.clear();
+    if (!valid_dtype(dtype)) return set_err(ctx, HPHI_E_INVAL, "unknown dtype %d", dtype);
+    if (nvec < 1 || nbatch < 0) return set_err(ctx, HPHI_E_INVAL, "nvec >= 1 and nbatch >= 0 required");
+    if (nbatch > 0 && (!x_host || !y_host)) return set_err(ctx, HPHI_E_INVAL, "x_host / y_host is NULL");
+    const int cpl = is_complex(dtype) ? 2 : 1;
+    if (nvec * cpl > kMaxCols) return set_err(ctx, HPHI_E_INVAL, "at most %d real columns per call", kMaxCols);
+    if (ham->device != ctx->device) return set_err(ctx, HPHI_E_INVAL, "hamiltonian belongs to another device");
+    const size_t bytes = (size_t)ham->D * nvec * cpl * real_size(real_of(dtype));
+    if (overlaps(x_host, bytes * nbatch, y_host, bytes * nbatch)) return set_err(ctx, HPHI_E_INVAL, "x and y overlap");
+    if (nbatch == 0) return HPHI_OK;
+    HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    int st = ensure_io(ctx, bytes);
+    if (st) return st;
+    cudaStream_t comp = ctx->stream, up = ctx->io_stream[0], down = ctx->io_stream[1];
+    // events: [0] start of the call on the compute stream, [1 + s] x slot s on the
+    // device, [3 + s] product of slot s done, [5 + s] y slot s copied back
+    cudaEvent_t *ev = ctx->io_ev;
+    HPHI_CUDA(ctx, cudaEventRecord(ev[0], comp));  // buffers free of earlier work on the stream
+    HPHI_CUDA(ctx, cudaStreamWaitEvent(up, ev[0], 0));
+    HPHI_CUDA(ctx, cudaStreamWaitEvent(down, ev[0], 0));
+    const char *xh = (const char *)x_host;
+    char *yh = (char *)y_host;
+    for (int64_t b = 0; b < nbatch && !st; b++) {
+        const int s = (int)(b & 1);
+        void *xd = ctx->io[s], *yd = ctx->io[2 + s];
+        // x_b up once the product of b - 2 has read the slot
+        if (b >= 2) HPHI_CUDA(ctx, cudaStreamWaitEvent(up, ev[3 + s], 0));
+        HPHI_CUDA(ctx, cudaMemcpyAsync(xd, xh + b * bytes, bytes, cudaMemcpyHostToDevice, up));
+        HPHI_CUDA(ctx, cudaEventRecord(ev[1 + s], up));
+        // product once x_b is there and y_{b-2} has left the slot
+        HPHI_CUDA(ctx, cudaStreamWaitEvent(comp, ev[1 + s], 0));
+        if (b >= 2) HPHI_CUDA(ctx, cudaStreamWaitEvent(comp, ev[5 + s], 0));
+        st = hphi_apply_H(ctx, ham, dtype, nvec, xd, nvec, yd, nvec, alpha, 0.0);
+        if (st) break;
+        HPHI_CUDA(ctx, cudaEventRecord(ev[3 + s], comp));
+        // y_b down after its product
+        HPHI_CUDA(ctx, cudaStreamWaitEvent(down, ev[3 + s], 0));
+        HPHI_CUDA(ctx, cudaMemcpyAsync(yh + b * bytes, yd, bytes, cudaMemcpyDeviceToHost, down));
+        HPHI_CUDA(ctx, cudaEventRecord(ev[5 + s], down));
+    }
+    // the caller's stream resumes after the last copy back; the call returns with
+    // every y_b on the host
+    cudaError_t e1 = cudaStreamSynchronize(up), e2 = cudaStreamSynchronize(down), e3 = cudaStreamSynchronize(comp);
+    if (st) return st;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return cuda_err(ctx, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "hphi_apply_H_host");
+    return HPHI_OK;
 }
 
 extern "C" int hphi_dot(hphi_ctx *ctx, int dtype, int64_t n, int nvec, const void *x, int64_t ldx, const void *y,

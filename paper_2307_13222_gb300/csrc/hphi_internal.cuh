@@ -120,6 +120,12 @@ struct hphi_ctx {
     void *vec[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t vec_bytes = 0;
     int *dflag = nullptr;        // device status word of consistency checks
+    // streaming H*x on host vectors: two x and two y device buffers, copy
+    // streams (host to device, device to host) and their ordering events
+    void *io[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t io_bytes = 0;
+    cudaStream_t io_stream[2] = {nullptr, nullptr};
+    cudaEvent_t io_ev[7] = {};
     // kernel timing: event pairs recorded around launches while profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_free;

@@ -100,6 +100,7 @@ _SIGS = {
     "hphi_ham_get_tuning": (i32, [vp, i32, C.POINTER(i32)]),
     "hphi_ham_autotune": (i32, [vp, vp, i32, i32, i32, C.POINTER(dbl), C.POINTER(i32)]),
     "hphi_apply_H": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, dbl, dbl]),
+    "hphi_apply_H_host": (i32, [vp, vp, i32, i32, i64, vp, vp, dbl]),
     "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
     "hphi_dot": (i32, [vp, i32, i64, i32, vp, i64, vp, i64, vp]),
     "hphi_nrm2": (i32, [vp, i32, i64, i32, vp, i64, vp]),
@@ -326,6 +327,28 @@ def hphi_apply_H(ham: Hamiltonian, x, y, alpha: float = 1.0, beta: float = 0.0):
     ctx._sync_stream()
     ctx.check(ctx.lib.hphi_apply_H(ctx.h, ham.h, _dtype_code(x), nv, px, ldx, py, ldy, float(alpha), float(beta)))
     return y
+
+
+def hphi_apply_H_host(ham: Hamiltonian, x_host, y_host, alpha: float = 1.0):
+    """y_b <- alpha H x_b for a batch of HOST vectors: x_host, y_host are CPU
+    tensors of shape [nbatch, D] or [nbatch, D, nvec], contiguous, same dtype
+    (pinned memory gives full copy speed).  Copies and products overlap inside
+    the library; returns when y_host is complete."""
+    import torch
+    ctx = ham.ctx
+    if x_host.device.type != "cpu" or y_host.device.type != "cpu":
+        raise ValueError("x_host and y_host must be host (CPU) tensors")
+    if x_host.dtype != y_host.dtype or x_host.shape != y_host.shape:
+        raise ValueError("x_host and y_host must have the same dtype and shape")
+    if x_host.dim() not in (2, 3) or x_host.shape[1] != ham.basis.dim:
+        raise ValueError("expected shape [nbatch, D] or [nbatch, D, nvec] with D = %d" % ham.basis.dim)
+    if not (x_host.is_contiguous() and y_host.is_contiguous()):
+        raise ValueError("x_host and y_host must be contiguous")
+    nv = 1 if x_host.dim() == 2 else int(x_host.shape[2])
+    ctx._sync_stream()
+    ctx.check(ctx.lib.hphi_apply_H_host(ctx.h, ham.h, _dtype_code(x_host), nv, int(x_host.shape[0]),
+                                        C.c_void_p(x_host.data_ptr()), C.c_void_p(y_host.data_ptr()), float(alpha)))
+    return y_host
 
 
 def hphi_dot(ctx: Context, x, y) -> np.ndarray:
