@@ -40,12 +40,26 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def source_tag() -> str:
+    """Short hash of the library's sources: hphi_last_kernel appends it to the
+    kernel name, so a profile taken on other sources does not match."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "hphi.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:10]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     nvcc = _nvcc()
     os.makedirs(OUT, exist_ok=True)
-    inc = ["-I", os.path.join(ROOT, "include")]
+    inc = ["-I", os.path.join(ROOT, "include"), f"-DHPHI_SRC_TAG=\"{source_tag()}\""]
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))

@@ -384,13 +384,13 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
             set_traversal(ctx, ham, a.P, (double)nc * sizeof(T) < 4.0 ? 4.0 : (double)nc * sizeof(T));
             a.P.split = ham->tune_split;
             st = launch_fly<T>(ctx, ham, a, fG, fcpl, red_mode, &grid);
-            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvo/k_hvc<%s,G%d,CPL%d,RED%d,coop%d>", tname<T>(),
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvo/k_hvc<%s,G%d,CPL%d,RED%d,coop%d>@" HPHI_SRC_TAG, tname<T>(),
                      fG, fcpl, red_mode, ham->tune_coop);
         } else if (cpl) {
             set_traversal(ctx, ham, a.P, (double)cpl * sizeof(T) < 4.0 ? 4.0 : (double)cpl * sizeof(T));
             a.P.split = ham->tune_split;
             st = launch_lean<T>(ctx, ham, a, cpl, ldc, red_mode, &grid);
-            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvl<%s,CPL%d,LDC%d,RED%d>", tname<T>(), cpl, ldc,
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvl<%s,CPL%d,LDC%d,RED%d>@" HPHI_SRC_TAG, tname<T>(), cpl, ldc,
                      red_mode);
         } else {
             bool pair_ok = nc == 2 && (L.ldx % 2 == 0) && (L.ldy % 2 == 0) && (!L.v || L.ldv % 2 == 0) &&
@@ -400,7 +400,7 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
                            (!L.v || (L.ldv * sizeof(T)) % vb == 0) && aligned(xs, vb) && aligned(ys, vb) &&
                            aligned(vs, vb);
             st = dispatch<T>(ctx, ham, a, pair_ok, quad_ok, &grid);
-            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hv<%s,NC%d>", tname<T>(), nc);
+            snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hv<%s,NC%d>@" HPHI_SRC_TAG, tname<T>(), nc);
         }
         if (st) return st;
         L.sgrid[L.nslice] = grid;

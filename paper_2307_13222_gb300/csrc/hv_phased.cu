@@ -4,8 +4,8 @@
 // with high half h: rows base .. base + len - 1, low halves of popcount p)
 // first copies the block's slice of x into shared memory.  It then builds
 // (H x) of the block in a second shared array, one bond at a time:
-//   1. the diagonal and the high-high bonds, row by row (their targets sit at
-//      the same row offset in block h ^ m: coalesced loads);
+//   1. the diagonal and the high-high bonds, two rows per lane at a time
+//      (their targets sit at the same row offset in block h ^ m: coalesced);
 //   2. each low-low bond k = (i, j): acc[q] += c_k xs[q'] over the list of the
 //      rows of class p whose bits i and j differ, q' = Lin's rank of the
 //      flipped low half (same class, so the target is in shared memory);
@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
     const T be = (T)a.beta;
     const bool use_beta = a.beta != 0.0, use_v = a.v != nullptr;
     constexpr int NR = RED == 2 ? 3 : (RED ? 1 : 0);
-    RedAcc<T> racc[NR > 0 ? NR : 1];
     constexpr int W = NT / 32, RPW = kPhRanges / W;
     static_assert(kPhRanges % W == 0, "row ranges must split evenly over the warps");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -58,6 +57,10 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
     const uint32_t ld = (uint32_t)a.ldx;
     const uint32_t *__restrict__ ent = P.ph_ent;
     constexpr int OS = kPhRanges + 1;  // offsets per list group
+    // reductions: each warp folds its rows of a block into its slots of red_sm
+    // (lane 0 owns them), so no accumulator stays live through the bond phases
+    if (RED != 0 && lane == 0)
+        for (int r = 0; r < 3; r++) red_sm[warp * 3 + r] = 0.0;
 
     for (int64_t c = blockIdx.x; c < P.nh; c += gridDim.x) {
         const int64_t h = block_of(P, c);
@@ -70,51 +73,78 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
         __syncthreads();
         const uint32_t q0 = (uint32_t)(((uint64_t)len * (uint32_t)(warp * RPW)) / kPhRanges);
         const uint32_t q1 = (uint32_t)(((uint64_t)len * (uint32_t)((warp + 1) * RPW)) / kPhRanges);
-        // 1. diagonal and high-high bonds
+        // 1. diagonal and high-high bonds, two rows per lane at a time (twice the
+        // gathers in flight)
         const int nhh = hb.nhh;
-        for (uint32_t q = q0 + lane; q < q1; q += 32) {
-            const uint32_t cp = cp0 + q;
-            const uint32_t l = __ldg(P.lstate + cp);
-            T d = __ldg(dlow + cp) + hb.dh;
-            for (int g = 0; g < P.ngroups; g++) d += hb.tab[g][(l >> (8 * g)) & 255u];
-            T acc = d * xs[q];
-            const uint32_t row = base + q;
+        for (uint32_t q = q0 + lane; q < q1; q += 64) {
+            const bool two = q + 32 < q1;
+            T acc[2];
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const uint32_t qq = q + 32 * t;
+                acc[t] = 0;
+                if (t == 0 || two) {
+                    const uint32_t cp = cp0 + qq;
+                    const uint32_t l = __ldg(P.lstate + cp);
+                    T d = __ldg(dlow + cp) + hb.dh;
+                    for (int g = 0; g < P.ngroups; g++) d += hb.tab[g][(l >> (8 * g)) & 255u];
+                    acc[t] = d * xs[qq];
+                }
+            }
             for (int k0 = 0; k0 < nhh; k0 += kPhGathers) {
-                T v[kPhGathers];
+                T v[2][kPhGathers];
 #pragma unroll
                 for (int u = 0; u < kPhGathers; u++) {
                     const int k = k0 + u;
-                    if (k < nhh)
-                        v[u] = gload<T>(X + (row + (uint32_t)hb.hh_delta[k]) * ld, hb.hh_outer[k] ? stream : keep);
+                    if (k < nhh) {
+                        const uint32_t off = (uint32_t)hb.hh_delta[k];
+                        const uint64_t pol = hb.hh_outer[k] ? stream : keep;
+                        v[0][u] = gload<T>(X + (base + q + off) * ld, pol);
+                        if (two) v[1][u] = gload<T>(X + (base + q + 32 + off) * ld, pol);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < kPhGathers; u++)
-                    if (k0 + u < nhh) acc = fma(hb.hh_coef[k0 + u], v[u], acc);
-            }
-            acs[q] = acc;
-        }
-        __syncwarp();
-        // 2. low-low bonds, targets in shared memory
-        const int32_t *o = P.ph_off + (int64_t)p * nll * OS + warp * RPW;
-        for (int k = 0; k < nll; k++, o += OS) {
-            const int32_t s0 = __ldg(o), s1 = __ldg(o + RPW);
-            if (s0 == s1) continue;
-            const T ck = ll_c[k];
-            for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
-                uint32_t pk[kPhUnroll];
-#pragma unroll
-                for (int u = 0; u < kPhUnroll; u++) {
-                    const int32_t i = i0 + 32 * u;
-                    pk[u] = i < s1 ? __ldg(ent + i) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < kPhUnroll; u++)
-                    if (i0 + 32 * u < s1) {
-                        const uint32_t q = pk[u] & 0xFFFFu;
-                        acs[q] = fma(ck, xs[pk[u] >> 16], acs[q]);
+                    if (k0 + u < nhh) {
+                        const T c = hb.hh_coef[k0 + u];
+                        acc[0] = fma(c, v[0][u], acc[0]);
+                        if (two) acc[1] = fma(c, v[1][u], acc[1]);
                     }
             }
-            __syncwarp();
+            acs[q] = acc[0];
+            if (two) acs[q + 32] = acc[1];
+        }
+        __syncwarp();
+        // 2. low-low bonds, targets in shared memory.  Lane j holds the list range
+        // of bond k0 + j; the bond loop takes it by shuffle.
+        for (int k0 = 0; k0 < nll; k0 += 32) {
+            int32_t my0 = 0, my1 = 0;
+            if (k0 + lane < nll) {
+                const int32_t *o = P.ph_off + ((int64_t)p * nll + k0 + lane) * OS + warp * RPW;
+                my0 = __ldg(o);
+                my1 = __ldg(o + RPW);
+            }
+            const int kn = nll - k0 < 32 ? nll - k0 : 32;
+            for (int j = 0; j < kn; j++) {
+                const int32_t s0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
+                if (s0 == s1) continue;
+                const T ck = ll_c[k0 + j];
+                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
+                    uint32_t pk[kPhUnroll];
+#pragma unroll
+                    for (int u = 0; u < kPhUnroll; u++) {
+                        const int32_t i = i0 + 32 * u;
+                        pk[u] = i < s1 ? __ldg(ent + i) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPhUnroll; u++)
+                        if (i0 + 32 * u < s1) {
+                            const uint32_t q = pk[u] & 0xFFFFu;
+                            acs[q] = fma(ck, xs[pk[u] >> 16], acs[q]);
+                        }
+                }
+                __syncwarp();
+            }
         }
         // 3. mixed bonds, targets in block h ^ 2^a
         const int nlh = hb.nlh;
@@ -148,6 +178,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
             __syncwarp();
         }
         // 4. epilogue over the warp's rows
+        RedAcc<T> racc[NR > 0 ? NR : 1];
         for (uint32_t q = q0 + lane; q < q1; q += 32) {
             const T acc = acs[q];
             const T xo = xs[q];
@@ -165,15 +196,17 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
             }
             if constexpr (RED == 3) racc[0].add(out, out);
         }
+        if constexpr (RED != 0) {
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                double val = racc[r].value();
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+                if (lane == 0) red_sm[warp * 3 + r] += val;
+            }
+        }
     }
     if constexpr (RED != 0) {
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-            double val = racc[r].value();
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
-            if (lane == 0) red_sm[warp * 3 + r] = val;
-        }
         __syncthreads();
         if (threadIdx.x < 3) {
             const int r = threadIdx.x;
@@ -205,7 +238,7 @@ int go_p(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
     *grid_out = (int)g;
     const int slot = prof_begin(ctx, PROF_HV);
     k_hvp<T, NT, RED, MINB><<<(int)g, NT, dyn, ctx->stream>>>(a, xs_len);
-    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvp<%s,%d,RED%d,MINB%d>", tname<T>(), NT, RED, MINB);
+    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvp<%s,%d,RED%d,MINB%d>@" HPHI_SRC_TAG, tname<T>(), NT, RED, MINB);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;

@@ -218,7 +218,7 @@ int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
     *grid_out = (int)g;
     const int slot = prof_begin(ctx, PROF_HV);
     k_hvs<T, RED, TAB, MINB><<<(int)g, kStagedThreads, dyn, ctx->stream>>>(a, xs_len);
-    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvs<%s,RED%d,TAB%d,MINB%d>", tname<T>(), RED, TAB, MINB);
+    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_hvs<%s,RED%d,TAB%d,MINB%d>@" HPHI_SRC_TAG, tname<T>(), RED, TAB, MINB);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;

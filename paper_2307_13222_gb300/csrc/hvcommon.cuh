@@ -73,6 +73,10 @@ __device__ __forceinline__ void cstore(T *p, uint64_t pol, T v) {
         asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 }
 
+#ifndef HPHI_SRC_TAG
+#define HPHI_SRC_TAG "untagged"
+#endif
+
 template <typename T>
 inline const char *tname() { return std::is_same<T, float>::value ? "f32" : "f64"; }
 
