@@ -146,36 +146,47 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
                 __syncwarp();
             }
         }
-        // 3. mixed bonds, targets in block h ^ 2^a
+        // 3. mixed bonds, targets in block h ^ 2^a.  Lane j holds the list range
+        // of mixed bond k0 + j of this block.
         const int nlh = hb.nlh;
-        const int32_t *om = P.ph_off + P.ph_mx0 + warp * RPW;
-        for (int k = 0; k < nlh; k++) {
-            const int g = (p * P.ph_nlb + hb.lh_bi[k]) * 2 + hb.lh_need[k];
-            const int32_t s0 = __ldg(om + (int64_t)g * OS), s1 = __ldg(om + (int64_t)g * OS + RPW);
-            // a non-empty list implies a valid target block
-            if (s0 == s1 || hb.lh_base[k] < 0) continue;
-            const T cf = hb.lh_coef[k];
-            const uint32_t b2 = (uint32_t)hb.lh_base[k];
-            const uint64_t pol = hb.lh_outer[k] ? stream : keep;
-            for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
-                uint32_t pk[kPhUnroll];
-                T v[kPhUnroll];
-#pragma unroll
-                for (int u = 0; u < kPhUnroll; u++) {
-                    const int32_t i = i0 + 32 * u;
-                    pk[u] = i < s1 ? __ldg(ent + i) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < kPhUnroll; u++)
-                    if (i0 + 32 * u < s1) v[u] = gload<T>(X + (b2 + (pk[u] >> 16)) * ld, pol);
-#pragma unroll
-                for (int u = 0; u < kPhUnroll; u++)
-                    if (i0 + 32 * u < s1) {
-                        const uint32_t q = pk[u] & 0xFFFFu;
-                        acs[q] = fma(cf, v[u], acs[q]);
-                    }
+        for (int k0 = 0; k0 < nlh; k0 += 32) {
+            int32_t my0 = 0, my1 = 0;
+            if (k0 + lane < nlh) {
+                const int k = k0 + lane;
+                const int g = (p * P.ph_nlb + hb.lh_bi[k]) * 2 + hb.lh_need[k];
+                const int32_t *o = P.ph_off + P.ph_mx0 + (int64_t)g * OS + warp * RPW;
+                my0 = __ldg(o);
+                my1 = __ldg(o + RPW);
             }
-            __syncwarp();
+            const int kn = nlh - k0 < 32 ? nlh - k0 : 32;
+            for (int j = 0; j < kn; j++) {
+                const int k = k0 + j;
+                const int32_t s0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
+                // a non-empty list implies a valid target block
+                if (s0 == s1 || hb.lh_base[k] < 0) continue;
+                const T cf = hb.lh_coef[k];
+                const uint32_t b2 = (uint32_t)hb.lh_base[k];
+                const uint64_t pol = hb.lh_outer[k] ? stream : keep;
+                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
+                    uint32_t pk[kPhUnroll];
+                    T v[kPhUnroll];
+#pragma unroll
+                    for (int u = 0; u < kPhUnroll; u++) {
+                        const int32_t i = i0 + 32 * u;
+                        pk[u] = i < s1 ? __ldg(ent + i) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPhUnroll; u++)
+                        if (i0 + 32 * u < s1) v[u] = gload<T>(X + (b2 + (pk[u] >> 16)) * ld, pol);
+#pragma unroll
+                    for (int u = 0; u < kPhUnroll; u++)
+                        if (i0 + 32 * u < s1) {
+                            const uint32_t q = pk[u] & 0xFFFFu;
+                            acs[q] = fma(cf, v[u], acs[q]);
+                        }
+                }
+                __syncwarp();
+            }
         }
         // 4. epilogue over the warp's rows
         RedAcc<T> racc[NR > 0 ? NR : 1];
