@@ -104,10 +104,10 @@ HPHI_API void hphi_ctx_destroy(hphi_ctx *ctx);
 /* Message of the last failing call on this context ("" if none). */
 HPHI_API const char *hphi_last_error(const hphi_ctx *ctx);
 /* Name of the last H*x kernel this context launched, with the template
- * arguments that select its code path and a hash of the library's sources
+ * arguments that select its code path and a hash of the H*x kernel sources
  * (e.g. "k_hvp<f32,512,RED1,MINB2>@0123456789"); "" before the first
  * launch.  For matching profiles to launches: a profile taken on other
- * sources carries another hash. */
+ * kernel sources carries another hash. */
 HPHI_API const char *hphi_last_kernel(const hphi_ctx *ctx);
 /* Number of SMs of the context's device (grid sizing information). */
 HPHI_API int hphi_ctx_sm_count(const hphi_ctx *ctx);

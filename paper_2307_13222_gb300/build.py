@@ -40,17 +40,19 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# sources that decide the code and tables of the H*x kernels
+HV_SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu",
+              "hvcommon.cuh", "rowvisit.cuh", "hphi_internal.cuh"]
+
+
 def source_tag() -> str:
-    """Short hash of the library's sources: hphi_last_kernel appends it to the
-    kernel name, so a profile taken on other sources does not match."""
+    """Short hash of the H*x kernel sources: hphi_last_kernel appends it to the
+    kernel name, so a profile taken on other kernel sources does not match."""
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(CSRC, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
-    with open(os.path.join(ROOT, "include", "hphi.h"), "rb") as fh:
-        h.update(fh.read())
+    for f in HV_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:10]
 
 
