@@ -268,8 +268,9 @@ __global__ void k_copy(int64_t n, int nr, const T *x, int64_t ldx, T *y, int64_t
     }
 }
 
-// c[j] partials = sum over this block's rows of V[j][r] * w[r], j in a chunk of
-// 8 stored vectors (grid.y walks the chunks).  V holds nv vectors of length n,
+// FP64 data: c[j] partials = sum over this block's rows of V[j][r] * w[r], j in
+// a chunk of 8 stored vectors (grid.y walks the chunks), one accumulator per
+// thread and vector, so the FP64 pipe does one FMA per element.  V holds nv vectors of length n,
 // vector j at V + j * n.  Fixed grid and order: deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_mdot(int64_t n, int nv, const T *__restrict__ V, const T *__restrict__ w,
@@ -300,16 +301,77 @@ __global__ void __launch_bounds__(kVT) k_mdot(int64_t n, int nv, const T *__rest
     }
 }
 
-// w[r] -= sum_j c[j] V[j][r] (c on the device, FP64; accumulated in T)
+// Multi-vector kernels of the reorthogonalisation (V holds nv vectors of
+// length n, vector j at V + j * n), tiled by rows: a thread
+// holds kMR rows of a tile of kMT * kMR rows, so every pass reads each V_j and w
+// once from memory.
+constexpr int kMT = 256, kMR = 4;
+
+// FP32 data: partials[block][j] = sum over the block's tiles of <V_j, w>.  Per
+// tile and vector the warp sums its 128 products in FP32, and lane 0 adds the
+// sum to the warp's FP64 slot; the block then sums its warps in order
+// (deterministic).
 template <typename T>
-__global__ void k_maxpy(int64_t n, int nv, const T *__restrict__ V, const double *__restrict__ c, T *w) {
-    __shared__ T cs[1024];
-    for (int j = threadIdx.x; j < nv && j < 1024; j += blockDim.x) cs[j] = (T)c[j];
+__global__ void __launch_bounds__(kMT) k_mdot_tiled(int64_t n, int nv, const T *__restrict__ V,
+                                                    const T *__restrict__ w, double *partials) {
+    extern __shared__ double acc_sm[];  // [kMT / 32][nv]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < (kMT / 32) * nv; j += kMT) acc_sm[j] = 0.0;
     __syncthreads();
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        T acc = (T)0;
-        for (int j = 0; j < nv; j++) acc = fma(cs[j], V[(int64_t)j * n + r], acc);
-        w[r] -= acc;
+    constexpr int64_t TILE = (int64_t)kMT * kMR;
+    const int64_t ntiles = (n + TILE - 1) / TILE;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = t * TILE + threadIdx.x;
+        T wv[kMR];
+#pragma unroll
+        for (int i = 0; i < kMR; i++) wv[i] = r0 + i * kMT < n ? w[r0 + i * kMT] : (T)0;
+#pragma unroll 2
+        for (int j = 0; j < nv; j++) {
+            const T *vj = V + (int64_t)j * n;
+            T p = (T)0;
+#pragma unroll
+            for (int i = 0; i < kMR; i++)
+                if (r0 + i * kMT < n) p = fma(vj[r0 + i * kMT], wv[i], p);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+            if (lane == 0) acc_sm[warp * nv + j] += (double)p;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nv; j += kMT) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < kMT / 32; w2++) sum += acc_sm[w2 * nv + j];
+        partials[(int64_t)blockIdx.x * nv + j] = sum;
+    }
+}
+
+// w[r] -= sum_j c[j] V[j][r], the sum in T in order of j, kMR rows per thread
+// so that 4 loads per vector are in flight.
+template <typename T>
+__global__ void __launch_bounds__(kMT) k_maxpy_tiled(int64_t n, int nv, const T *__restrict__ V,
+                                                     const double *__restrict__ c, T *w) {
+    extern __shared__ __align__(16) unsigned char cs_raw[];
+    T *cs = (T *)cs_raw;  // [nv]
+    for (int j = threadIdx.x; j < nv; j += kMT) cs[j] = (T)c[j];
+    __syncthreads();
+    constexpr int64_t TILE = (int64_t)kMT * kMR;
+    const int64_t ntiles = (n + TILE - 1) / TILE;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = t * TILE + threadIdx.x;
+        T acc[kMR];
+#pragma unroll
+        for (int i = 0; i < kMR; i++) acc[i] = (T)0;
+#pragma unroll 4
+        for (int j = 0; j < nv; j++) {
+            const T *vj = V + (int64_t)j * n;
+            const T cj = cs[j];
+#pragma unroll
+            for (int i = 0; i < kMR; i++)
+                if (r0 + i * kMT < n) acc[i] = fma(cj, vj[r0 + i * kMT], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kMR; i++)
+            if (r0 + i * kMT < n) w[r0 + i * kMT] -= acc[i];
     }
 }
 
@@ -417,34 +479,49 @@ int launch_lincomb(hphi_ctx *ctx, LinComb &L) {
 }
 
 int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const void *w, double *out_dev) {
-    int64_t gx = (n + kVT - 1) / kVT;
-    const int64_t cap = (int64_t)ctx->sm_count * 4;
-    if (gx > cap) gx = cap;
-    if (gx < 1) gx = 1;
-    const int gy = (nv + 7) / 8;
-    int st = ensure_partials(ctx, (size_t)gx * nv);
-    if (st) return st;
-    const int slot = prof_begin(ctx, PROF_VEC);
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    if (real_dtype == HPHI_F64)
+    if (nv < 1 || nv > 1024) return set_err(ctx, HPHI_E_INVAL, "1 to 1024 stored vectors");
+    int st;
+    if (real_dtype == HPHI_F64) {
+        // per-tile warp sums would cost more FP64 adds than the products themselves
+        int64_t gx = (n + kVT - 1) / kVT;
+        if (gx > (int64_t)ctx->sm_count * 4) gx = (int64_t)ctx->sm_count * 4;
+        if (gx < 1) gx = 1;
+        if ((st = ensure_partials(ctx, (size_t)gx * nv))) return st;
+        const int slot = prof_begin(ctx, PROF_VEC);
+        dim3 grid((unsigned)gx, (unsigned)((nv + 7) / 8));
         k_mdot<double><<<grid, kVT, 0, ctx->stream>>>(n, nv, (const double *)V, (const double *)w, ctx->partials);
-    else
-        k_mdot<float><<<grid, kVT, 0, ctx->stream>>>(n, nv, (const float *)V, (const float *)w, ctx->partials);
+        prof_end(ctx, slot);
+        HPHI_CUDA(ctx, cudaGetLastError());
+        return reduce_partials(ctx, ctx->partials, (int)gx, nv, out_dev);
+    }
+    const int64_t tile = (int64_t)kMT * kMR;
+    int64_t g = (n + tile - 1) / tile;
+    if (g > (int64_t)ctx->sm_count * 8) g = (int64_t)ctx->sm_count * 8;
+    if (g < 1) g = 1;
+    if ((st = ensure_partials(ctx, (size_t)g * nv))) return st;
+    const size_t dyn = sizeof(double) * (kMT / 32) * nv;
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_mdot_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const int slot = prof_begin(ctx, PROF_VEC);
+    k_mdot_tiled<float><<<(unsigned)g, kMT, dyn, ctx->stream>>>(n, nv, (const float *)V, (const float *)w,
+                                                               ctx->partials);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
-    return reduce_partials(ctx, ctx->partials, (int)gx, nv, out_dev);
+    return reduce_partials(ctx, ctx->partials, (int)g, nv, out_dev);
 }
 
 int launch_maxpy(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const double *c_dev, void *w) {
-    if (nv > 1024) return set_err(ctx, HPHI_E_INVAL, "at most 1024 stored vectors");
-    int64_t g = (n + 255) / 256;
+    if (nv < 1 || nv > 1024) return set_err(ctx, HPHI_E_INVAL, "1 to 1024 stored vectors");
+    const int64_t tile = (int64_t)kMT * kMR;
+    int64_t g = (n + tile - 1) / tile;
     if (g > (int64_t)ctx->sm_count * 8) g = (int64_t)ctx->sm_count * 8;
     if (g < 1) g = 1;
     const int slot = prof_begin(ctx, PROF_VEC);
     if (real_dtype == HPHI_F64)
-        k_maxpy<double><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nv, (const double *)V, c_dev, (double *)w);
+        k_maxpy_tiled<double><<<(unsigned)g, kMT, sizeof(double) * nv, ctx->stream>>>(n, nv, (const double *)V, c_dev,
+                                                                                      (double *)w);
     else
-        k_maxpy<float><<<(unsigned)g, 256, 0, ctx->stream>>>(n, nv, (const float *)V, c_dev, (float *)w);
+        k_maxpy_tiled<float><<<(unsigned)g, kMT, sizeof(float) * nv, ctx->stream>>>(n, nv, (const float *)V, c_dev,
+                                                                                    (float *)w);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
     return HPHI_OK;
