@@ -538,7 +538,7 @@ def run_hubbard4x4(args):
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
         es = 4 if tdt == torch.float32 else 8
-        out[dt_name] = dict(ms=ms, r=r, roof=_roofline(ctx, 3.0 * es * b.dim, "k_hv (Hubbard, generic)"))
+        out[dt_name] = dict(ms=ms, r=r, roof=_roofline(ctx, 3.0 * es * b.dim, ctx.last_kernel()))
         del v0
         torch.cuda.empty_cache()
     ck = clocks.stop()

@@ -309,6 +309,45 @@ int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) 
     return HPHI_OK;
 }
 
+// Down-hop lists of the bond-major H*x kernel for Hubbard models (row block =
+// the D_dn rows of one up string): group g = coefficient index (a down hop
+// pair with one fermion sign), entries q | q' << 16 for the down states q that
+// hop to q' with that coefficient, ascending in q, with the segment starts of
+// kPhRanges row ranges as in the spin lists.  Built from the ELL tables; not
+// built when D_dn >= 2^16 or there are more than 128 coefficients.
+int build_hub_lists(hphi_ctx *ctx, hphi_ham *H) {
+    const int64_t L = H->L;
+    const int w = H->ll_w, nc = H->host.n_ncoef;
+    if (L >= 65536 || nc > 128 || w == 0) return HPHI_OK;
+    std::vector<uint8_t> cnt((size_t)L);
+    std::vector<uint32_t> tgt((size_t)L * w);
+    std::vector<uint16_t> cf((size_t)L * w);
+    HPHI_CUDA(ctx, cudaMemcpy(cnt.data(), H->ll_cnt, cnt.size(), cudaMemcpyDeviceToHost));
+    HPHI_CUDA(ctx, cudaMemcpy(tgt.data(), H->ll_tgt, tgt.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    HPHI_CUDA(ctx, cudaMemcpy(cf.data(), H->ll_cf, cf.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    std::vector<std::vector<uint32_t>> grp(nc);
+    for (int64_t q = 0; q < L; q++)
+        for (int e = 0; e < cnt[q]; e++) {
+            const size_t o = (size_t)e * L + q;
+            if (cf[o] < nc) grp[cf[o]].push_back((uint32_t)q | tgt[o] << 16);
+        }
+    std::vector<uint32_t> ent;
+    std::vector<int32_t> off;
+    for (int g = 0; g < nc; g++) {
+        size_t i = 0;
+        for (int r = 0; r < kPhRanges; r++) {
+            const uint32_t qe = (uint32_t)(((uint64_t)L * (uint32_t)(r + 1)) / kPhRanges);
+            off.push_back((int32_t)ent.size());
+            while (i < grp[g].size() && (grp[g][i] & 0xFFFFu) < qe) ent.push_back(grp[g][i++]);
+        }
+        off.push_back((int32_t)ent.size());
+    }
+    H->ph_mx0 = (int64_t)off.size();
+    int st;
+    if ((st = to_dev(ctx, &H->ph_ent, ent)) || (st = to_dev(ctx, &H->ph_off, off))) return st;
+    return HPHI_OK;
+}
+
 int build_hubbard(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) {
     const hphi_basis *B = H->basis;
     const int N = B->N;
@@ -407,7 +446,7 @@ int build_hubbard(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_term
     cudaFree(d_h1);
     cudaFree(d_v);
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_hub_tables");
-    return HPHI_OK;
+    return build_hub_lists(ctx, H);
 }
 
 }  // namespace

@@ -303,11 +303,14 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         const T *vs = L.v ? (const T *)L.v + c0 : nullptr;
         // spin sector, one column: the staged kernels (variants 2 and 3), automatic there
         // (measured faster than the table-driven kernel on the 6x5 and 4x8 sectors)
-        const bool staged = (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
-                            ham->model == HPHI_SPIN_HALF &&
-                            ham->nlo <= 16 &&
-                            ham->host.n_ll <= 128 && same_ld && red_mode >= 0 && L.ldx == 1 && L.ncol == 1 &&
-                            !L.swap && (double)ham->D < 4294967296.0;
+        const bool one_col = same_ld && red_mode >= 0 && L.ldx == 1 && L.ncol == 1 && !L.swap &&
+                             (double)ham->D < 4294967296.0;
+        const bool spin_staged = (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
+                                 ham->model == HPHI_SPIN_HALF && ham->nlo <= 16 && ham->host.n_ll <= 128 && one_col;
+        // Hubbard, one column: the bond-major kernel where its down-hop lists exist
+        const bool hub_phased = (ham->tune_variant == 3 || ham->tune_variant < 0) && ham->model == HPHI_HUBBARD &&
+                                ham->ph_ent && one_col;
+        const bool staged = spin_staged || hub_phased;
         // spin models: the on-the-fly-rank kernel for unit / pair / 32-wide rows
         int fG = 0, fcpl = 0;
         // variant -1 (automatic): on-the-fly ranks for 32-wide rows, lists for unit / pair rows
@@ -376,8 +379,8 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
             a.P.split = 1;
             // automatic: the bond-major kernel where its lists exist (measured 14-42 % faster than
             // the staged kernel on the 6x5 and 4x8 sectors, FP32 and FP64)
-            const bool phased = ham->tune_variant == 3 || (ham->tune_variant < 0 && ham->ph_ent &&
-                                                           ham->host.n_ll <= 128);
+            const bool phased = hub_phased || ham->tune_variant == 3 ||
+                                (ham->tune_variant < 0 && ham->ph_ent && ham->host.n_ll <= 128);
             st = phased ? launch_phased<T>(ctx, ham, a, red_mode, &grid)
                         : launch_staged<T>(ctx, ham, a, red_mode, &grid);
         } else if (fG) {

@@ -1,4 +1,5 @@
-// Bond-major H*x kernel for the spin-1/2 S^z sector with one column.
+// Bond-major H*x kernel for the spin-1/2 S^z sector and for Hubbard models,
+// one column.
 //
 // Like the staged kernel, the thread block that owns row block h (the states
 // with high half h: rows base .. base + len - 1, low halves of popcount p)
@@ -20,7 +21,11 @@
 // carry offsets at the range boundaries), so consecutive phases are ordered by
 // __syncwarp() alone.  Every row sums its terms in a fixed order, so results
 // are deterministic.  (Sec. 3.1.1 and Sec. 5: the spin-1/2 exchange terms and
-// their action on the bit-encoded basis.)
+// their action on the bit-encoded basis.)  Hubbard models take the same path
+// with row block = the D_dn rows of one up string: phase 1 carries the
+// diagonal and the up hops (whole-block moves with the up string's sign),
+// phase 2 the down hops, one list per (hop pair, fermion sign) coefficient;
+// there is no phase 3.
 #include "hvcommon.cuh"
 
 namespace hphi {
@@ -41,8 +46,11 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
     __shared__ T ll_c[kPhMaxLL];
     const HvTables &P = a.P;
     const HamDesc &D = *P.desc;
-    const int nll = D.n_ll;
-    for (int i = threadIdx.x; i < nll; i += NT) ll_c[i] = (T)D.ll[i].cxy;
+    // Hubbard: the low-low lists are the down hops, one list per coefficient
+    // (hop pair and fermion sign), all in one class (p = 0)
+    const bool hub = P.model == kHubbard;
+    const int nll = hub ? D.n_ncoef : D.n_ll;
+    for (int i = threadIdx.x; i < nll; i += NT) ll_c[i] = (T)(hub ? D.coef[i] : D.ll[i].cxy);
     const uint64_t keep = spol(P.hints, 0), stream = spol(P.hints, 1);
     const T al = (T)(a.alpha_dev ? a.alpha_dev[0] : a.alpha[0]);
     const T ga = (T)(a.gamma_dev ? a.gamma_dev[0] : a.gamma[0]);
@@ -68,7 +76,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
         setup_block<T>(P, h, hb);
         if (!hb.valid) continue;
         const uint32_t base = (uint32_t)hb.base, len = hb.len, cp0 = hb.cp0;
-        const int p = P.n - __popcll((unsigned long long)h);
+        const int p = hub ? 0 : P.n - __popcll((unsigned long long)h);
         for (uint32_t q = threadIdx.x; q < len; q += NT) xs[q] = gload<T>(X + (base + q) * ld, keep);
         __syncthreads();
         const uint32_t q0 = (uint32_t)(((uint64_t)len * (uint32_t)(warp * RPW)) / kPhRanges);
@@ -85,7 +93,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
                 acc[t] = 0;
                 if (t == 0 || two) {
                     const uint32_t cp = cp0 + qq;
-                    const uint32_t l = __ldg(P.lstate + cp);
+                    const uint32_t l = hub ? __ldg(P.states_dn + qq) : __ldg(P.lstate + cp);
                     T d = __ldg(dlow + cp) + hb.dh;
                     for (int g = 0; g < P.ngroups; g++) d += hb.tab[g][(l >> (8 * g)) & 255u];
                     acc[t] = d * xs[qq];
@@ -262,7 +270,8 @@ int go_p(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
 // block of 1024 threads (206 KB).
 template <typename T>
 int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid) {
-    if (!a.P.ph_ent || ham->host.n_ll > kPhMaxLL)
+    const int nlists = ham->model == HPHI_HUBBARD ? ham->host.n_ncoef : ham->host.n_ll;
+    if (!a.P.ph_ent || nlists > kPhMaxLL)
         return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: no bond lists for this Hamiltonian");
     const uint32_t xl = staged_block_len(ham);
     constexpr bool F = std::is_same<T, float>::value;

@@ -226,9 +226,10 @@ int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len
 
 }  // namespace
 
-// Largest row block of a spin sector (the class of popcount closest to half of
-// the low bits that occurs).
+// Largest row block: of a spin sector, the class of popcount closest to half of
+// the low bits; of a Hubbard model, the D_dn rows of one up string.
 uint32_t staged_block_len(const hphi_ham *ham) {
+    if (ham->model == HPHI_HUBBARD) return (uint32_t)ham->basis->sp[1].dim;  // D_dn rows per up string
     const std::vector<uint32_t> &lo = ham->basis->sp[0].loff_h;
     uint32_t m = 0;
     for (size_t p = 0; p + 1 < lo.size(); p++) m = lo[p + 1] - lo[p] > m ? lo[p + 1] - lo[p] : m;

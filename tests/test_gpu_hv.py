@@ -160,11 +160,15 @@ def test_square_4x8_full_size_sampled(dtype):
     assert _sampled_rows(m, h, dtype, 1, rows, 42) < (1e-15 if dtype == torch.float64 else 1e-6)
 
 
-def test_hubbard_4x4_full_size_sampled():
+@pytest.mark.parametrize("variant", [-1, 0])
+def test_hubbard_4x4_full_size_sampled(variant):
+    """165,636,900 rows: the bond-major kernel (automatic) and the generic one."""
     m, b, h = pair("HUBBARD", 16, 8, 8, hubbard_terms(16, square(4, 4), t=1.0, U=8.0))
+    h.set_tuning(variant=variant)
     rng = np.random.default_rng(9)
     rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 300)])
     assert _sampled_rows(m, h, torch.float64, 1, rows, 43) < 1e-15
+    assert _sampled_rows(m, h, torch.float32, 1, rows, 44) < 1e-6
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -180,7 +184,7 @@ def test_rrg26_block32_full_size_sampled(dtype):
 
 @pytest.mark.parametrize("variant,split,hints,inner", [(-1, 1, 1, -1), (0, 1, 1, -1), (1, 1, 1, -1),
                                                        (0, 3, 0, 2), (1, 2, 0, 1), (1, 4, 1, 0), (-1, 8, 1, 32),
-                                                       (2, 1, 1, -1), (2, 1, 0, 3)])
+                                                       (2, 1, 1, -1), (2, 1, 0, 3), (3, 1, 1, -1)])
 @pytest.mark.parametrize("shape", ["sector", "full", "hubbard"])
 @pytest.mark.parametrize("nvec", [1, 2, 32])
 def test_kernel_variants_and_knobs(variant, split, hints, inner, shape, nvec):
