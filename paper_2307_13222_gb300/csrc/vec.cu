@@ -92,6 +92,18 @@ __global__ void k_reduce(const double *partials, int grid, int nval, double *out
     }
 }
 
+// out[v] = sum_b partials[b][v], one warp per value: lane l sums b = l, l + 32,
+// ... in order, then a fixed butterfly (deterministic).  For many values.
+__global__ void k_reduce_wide(const double *partials, int grid, int nval, double *out) {
+    const int v = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (v >= nval) return;
+    double sum = 0.0;
+    for (int b = lane; b < grid; b += 32) sum += partials[(int64_t)b * nval + v];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) out[v] = sum;
+}
+
 struct LCArgs {
     int64_t n;
     int nr, tpr, red;
@@ -308,11 +320,12 @@ __global__ void __launch_bounds__(kVT) k_mdot(int64_t n, int nv, const T *__rest
 constexpr int kMT = 256, kMR = 4;
 
 // FP32 data: partials[block][j] = sum over the block's tiles of <V_j, w>.  Per
-// tile and vector the warp sums its 128 products in FP32, and lane 0 adds the
-// sum to the warp's FP64 slot; the block then sums its warps in order
-// (deterministic).
+// tile, a lane forms its partial products for 32 vectors at a time (4 rows
+// each); a transposing butterfly (31 shuffles) leaves in lane l the warp's sum
+// for vector j0 + l, which lane l adds to the warp's FP64 slot.  The block then
+// sums its warps in order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(kMT) k_mdot_tiled(int64_t n, int nv, const T *__restrict__ V,
+__global__ void __launch_bounds__(kMT, 4) k_mdot_tiled(int64_t n, int nv, const T *__restrict__ V,
                                                     const T *__restrict__ w, double *partials) {
     extern __shared__ double acc_sm[];  // [kMT / 32][nv]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -325,16 +338,31 @@ __global__ void __launch_bounds__(kMT) k_mdot_tiled(int64_t n, int nv, const T *
         T wv[kMR];
 #pragma unroll
         for (int i = 0; i < kMR; i++) wv[i] = r0 + i * kMT < n ? w[r0 + i * kMT] : (T)0;
-#pragma unroll 2
-        for (int j = 0; j < nv; j++) {
-            const T *vj = V + (int64_t)j * n;
-            T p = (T)0;
+        for (int j0 = 0; j0 < nv; j0 += 32) {
+            T v[32];
 #pragma unroll
-            for (int i = 0; i < kMR; i++)
-                if (r0 + i * kMT < n) p = fma(vj[r0 + i * kMT], wv[i], p);
+            for (int j = 0; j < 32; j++) {
+                v[j] = (T)0;
+                if (j0 + j < nv) {
+                    const T *vj = V + (int64_t)(j0 + j) * n;
 #pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-            if (lane == 0) acc_sm[warp * nv + j] += (double)p;
+                    for (int i = 0; i < kMR; i++)
+                        if (r0 + i * kMT < n) v[j] = fma(vj[r0 + i * kMT], wv[i], v[j]);
+                }
+            }
+            // transposing butterfly: after the step of width s, lane l keeps the
+            // half of its values whose index offset matches bit s of l
+#pragma unroll
+            for (int s2 = 16; s2 >= 1; s2 >>= 1) {
+                const bool upper = (lane & s2) != 0;
+#pragma unroll
+                for (int j = 0; j < s2; j++) {
+                    const T send = upper ? v[j] : v[j + s2];
+                    const T keep = upper ? v[j + s2] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s2);
+                }
+            }
+            if (j0 + lane < nv) acc_sm[warp * nv + j0 + lane] += (double)v[0];
         }
     }
     __syncthreads();
@@ -504,9 +532,10 @@ int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V,
     const int slot = prof_begin(ctx, PROF_VEC);
     k_mdot_tiled<float><<<(unsigned)g, kMT, dyn, ctx->stream>>>(n, nv, (const float *)V, (const float *)w,
                                                                ctx->partials);
+    k_reduce_wide<<<(nv + 7) / 8, 256, 0, ctx->stream>>>(ctx->partials, (int)g, nv, out_dev);
     prof_end(ctx, slot);
     HPHI_CUDA(ctx, cudaGetLastError());
-    return reduce_partials(ctx, ctx->partials, (int)g, nv, out_dev);
+    return HPHI_OK;
 }
 
 int launch_maxpy(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V, const double *c_dev, void *w) {
