@@ -210,7 +210,7 @@ def measure_e2e(ctx, ham, dim, dtype_name, K):
     from paper_2307_13222_gb300 import hphi
     tdt = torch.float32 if dtype_name == "f32" else torch.float64
     es = 4 if dtype_name == "f32" else 8
-    nb = max(2, min(K, 4))
+    nb = max(2, min(K, 8))
     xh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     yh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     xd = torch.empty(dim, dtype=tdt, device="cuda")
