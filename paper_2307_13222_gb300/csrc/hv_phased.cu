@@ -155,45 +155,78 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
             }
         }
         // 3. mixed bonds, targets in block h ^ 2^a.  Lane j holds the list range
-        // of mixed bond k0 + j of this block.
+        // of mixed bond k0 + j of this block; the loop walks the batches of all
+        // of them in order, loading the next batch's entries before it gathers
+        // and adds the current one (the first batch of a bond no longer waits for
+        // its list after the previous bond ends).
         const int nlh = hb.nlh;
         for (int k0 = 0; k0 < nlh; k0 += 32) {
             int32_t my0 = 0, my1 = 0;
+            bool okb = false;
             if (k0 + lane < nlh) {
                 const int k = k0 + lane;
                 const int g = (p * P.ph_nlb + hb.lh_bi[k]) * 2 + hb.lh_need[k];
                 const int32_t *o = P.ph_off + P.ph_mx0 + (int64_t)g * OS + warp * RPW;
                 my0 = __ldg(o);
                 my1 = __ldg(o + RPW);
+                okb = my1 > my0 && hb.lh_base[k] >= 0;
             }
-            const int kn = nlh - k0 < 32 ? nlh - k0 : 32;
-            for (int j = 0; j < kn; j++) {
+            unsigned ne = __ballot_sync(0xffffffffu, okb);
+            if (!ne) continue;
+            int j = __ffs(ne) - 1;
+            ne &= ne - 1;
+            int32_t b0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
+            uint32_t pk[kPhUnroll];
+#pragma unroll
+            for (int u = 0; u < kPhUnroll; u++) {
+                const int32_t i = b0 + lane + 32 * u;
+                pk[u] = i < s1 ? __ldg(ent + i) : 0u;
+            }
+            while (true) {
+                int jn = j;
+                int32_t bn = b0 + 32 * kPhUnroll, s1n = s1;
+                bool more = true, sw = false;
+                if (bn >= s1) {
+                    if (ne) {
+                        jn = __ffs(ne) - 1;
+                        ne &= ne - 1;
+                        bn = __shfl_sync(0xffffffffu, my0, jn);
+                        s1n = __shfl_sync(0xffffffffu, my1, jn);
+                        sw = true;
+                    } else {
+                        more = false;
+                    }
+                }
                 const int k = k0 + j;
-                const int32_t s0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
-                // a non-empty list implies a valid target block
-                if (s0 == s1 || hb.lh_base[k] < 0) continue;
                 const T cf = hb.lh_coef[k];
                 const uint32_t b2 = (uint32_t)hb.lh_base[k];
                 const uint64_t pol = hb.lh_outer[k] ? stream : keep;
-                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
-                    uint32_t pk[kPhUnroll];
-                    T v[kPhUnroll];
+                T v[kPhUnroll];
 #pragma unroll
-                    for (int u = 0; u < kPhUnroll; u++) {
-                        const int32_t i = i0 + 32 * u;
-                        pk[u] = i < s1 ? __ldg(ent + i) : 0u;
-                    }
+                for (int u = 0; u < kPhUnroll; u++)
+                    if (b0 + lane + 32 * u < s1) v[u] = gload<T>(X + (b2 + (pk[u] >> 16)) * ld, pol);
+                uint32_t pn[kPhUnroll];
 #pragma unroll
-                    for (int u = 0; u < kPhUnroll; u++)
-                        if (i0 + 32 * u < s1) v[u] = gload<T>(X + (b2 + (pk[u] >> 16)) * ld, pol);
-#pragma unroll
-                    for (int u = 0; u < kPhUnroll; u++)
-                        if (i0 + 32 * u < s1) {
-                            const uint32_t q = pk[u] & 0xFFFFu;
-                            acs[q] = fma(cf, v[u], acs[q]);
-                        }
+                for (int u = 0; u < kPhUnroll; u++) {
+                    const int32_t i = bn + lane + 32 * u;
+                    pn[u] = (more && i < s1n) ? __ldg(ent + i) : 0u;
                 }
-                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++)
+                    if (b0 + lane + 32 * u < s1) {
+                        const uint32_t q = pk[u] & 0xFFFFu;
+                        acs[q] = fma(cf, v[u], acs[q]);
+                    }
+                if (!more) {
+                    __syncwarp();
+                    break;
+                }
+                if (sw) __syncwarp();
+                j = jn;
+                b0 = bn;
+                s1 = s1n;
+#pragma unroll
+                for (int u = 0; u < kPhUnroll; u++) pk[u] = pn[u];
             }
         }
         // 4. epilogue over the warp's rows
