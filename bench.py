@@ -228,9 +228,20 @@ def measure_e2e(ctx, ham, dim, dtype_name, K):
         hphi.hphi_apply_H_host(ham, xh, yh)
         calls.append((time.perf_counter() - t0) * 1e3 / nb)
     ms = statistics.median(calls)
-    del xh, yh
+    # this machine's host link, for reading the number: one plain copy each way
+    xd = torch.empty(dim, dtype=tdt, device="cuda")
+    link = {}
+    for name, fn in (("h2d_gbps", lambda: xd.copy_(xh[0], non_blocking=True)),
+                     ("d2h_gbps", lambda: yh[0].copy_(xd, non_blocking=True))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        link[name] = es * dim / (time.perf_counter() - t0) / 1e9
+    del xh, yh, xd
     torch.cuda.empty_cache()
-    return dict(value=2.0 * es * dim / (ms * 1e-3) / 1e9, ms=ms, h2d=es * dim, d2h=es * dim, batch=nb, calls=calls)
+    return dict(value=2.0 * es * dim / (ms * 1e-3) / 1e9, ms=ms, h2d=es * dim, d2h=es * dim, batch=nb, calls=calls,
+                link=link)
 
 
 def run_native(args):
@@ -321,7 +332,8 @@ def run_native(args):
     if e2e:
         line["e2e"] = {"value": e2e["value"], "unit": "GB/s", "h2d_bytes_per_step": e2e["h2d"],
                        "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"], "step": "hphi_apply_H_host",
-                       "vectors_per_call": e2e["batch"], "calls_ms_per_vector": e2e["calls"]}
+                       "vectors_per_call": e2e["batch"], "calls_ms_per_vector": e2e["calls"],
+                       "host_link": e2e["link"]}
     if other:
         a64 = 3.0 * 8 * dim / ((other["hv_ms"] / max(other["hv_launches"], 1)) * 1e-3) / 1e9
         line["fp64"] = {"value": other["value"], "ms_per_step": other["ms"] / max(2, K // 4),
