@@ -32,7 +32,9 @@ namespace hphi {
 
 namespace {
 
-constexpr int kPhUnroll = 4;   // list entries in flight per lane
+constexpr int kPhUnroll = 4;   // list entries in flight per lane (mixed phase; FP64 low-low phase)
+// low-low phase: FP32 takes 8 entries per lane per batch (measured 1.7 % faster)
+template <typename T> constexpr int kPhUnrollLL = sizeof(T) == 4 ? 8 : 4;
 constexpr int kPhGathers = 4;  // high-high gathers in flight per row
 constexpr int kPhMaxLL = 128;
 
@@ -137,15 +139,15 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
                 const int32_t s0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
                 if (s0 == s1) continue;
                 const T ck = ll_c[k0 + j];
-                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnroll) {
-                    uint32_t pk[kPhUnroll];
+                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnrollLL<T>) {
+                    uint32_t pk[kPhUnrollLL<T>];
 #pragma unroll
-                    for (int u = 0; u < kPhUnroll; u++) {
+                    for (int u = 0; u < kPhUnrollLL<T>; u++) {
                         const int32_t i = i0 + 32 * u;
                         pk[u] = i < s1 ? __ldg(ent + i) : 0u;
                     }
 #pragma unroll
-                    for (int u = 0; u < kPhUnroll; u++)
+                    for (int u = 0; u < kPhUnrollLL<T>; u++)
                         if (i0 + 32 * u < s1) {
                             const uint32_t q = pk[u] & 0xFFFFu;
                             acs[q] = fma(ck, xs[pk[u] >> 16], acs[q]);
