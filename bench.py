@@ -200,6 +200,23 @@ def measure_dtype(ctx, ham, dim, dtype_name, K, W, dist, world):
                 vec_launches=vec_n, vec_ms=vec_ms, e0=r["e0"], steps=r["steps"], es=es)
 
 
+def traffic_for(path, kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, or None unless the
+    summary's `kernel:` line names exactly the kernel instance that ran (its
+    template arguments and the hash of the H*x sources it was built from)."""
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.split(":")[0] in ("kernel", "bytes_per_launch"):
+                k, v = ln.split(":", 1)
+                rec[k] = v.strip()
+    if rec.get("kernel") == kernel_name and "bytes_per_launch" in rec:
+        return float(rec["bytes_per_launch"])
+    return None
+
+
 def measure_e2e(ctx, ham, dim, dtype_name, K):
     """H*x through the public API with HOST buffers: one hphi_apply_H_host call
     over a batch of pinned host vectors.  The timed call (wall clock) includes,
@@ -289,17 +306,8 @@ def run_native(args):
     achieved = kern_bytes / (hv_avg_ms * 1e-3) / 1e9
     # DRAM bytes per launch of this kernel from the committed ncu summary: null
     # unless the summary names exactly the kernel instance that ran here
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"hv_fused_square4x8_{args.dtype}_traffic.md")
-    if os.path.exists(tfile):
-        rec = {}
-        with open(tfile) as f:
-            for ln in f:
-                if ":" in ln and ln.split(":")[0] in ("kernel", "bytes_per_launch"):
-                    k, v = ln.split(":", 1)
-                    rec[k] = v.strip()
-        if rec.get("kernel") == kernel_name and "bytes_per_launch" in rec:
-            traffic = float(rec["bytes_per_launch"])
+    traffic = traffic_for(os.path.join(ROOT, "profiles", f"hv_fused_square4x8_{args.dtype}_traffic.md"),
+                          kernel_name)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O

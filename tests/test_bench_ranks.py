@@ -60,3 +60,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
         steps, warmup, gpus = 2, 3, 2
     assert bench.run_reference(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel(tmp_path):
+    """The roofline's DRAM traffic comes from a committed ncu summary only when
+    the summary names the exact kernel instance (arguments and source hash)."""
+    import bench
+    f = tmp_path / "t.md"
+    f.write_text("text\nkernel: k_hvp<f32,512,RED1,MINB2>@0123456789\nbytes_per_launch: 123\n")
+    assert bench.traffic_for(str(f), "k_hvp<f32,512,RED1,MINB2>@0123456789") == 123.0
+    assert bench.traffic_for(str(f), "k_hvp<f32,512,RED1,MINB2>@9876543210") is None
+    assert bench.traffic_for(str(f), "k_hvs<f32,RED1,TAB1,MINB3>@0123456789") is None
+    assert bench.traffic_for(str(tmp_path / "missing.md"), "x") is None
+
+
+def test_source_tag_tracks_the_kernel_sources():
+    import importlib
+    build = importlib.import_module("paper_2307_13222_gb300.build")
+    t = build.source_tag()
+    assert len(t) == 10 and all(c in "0123456789abcdef" for c in t)
+    assert "hv_phased.cu" in build.HV_SOURCES and all(f in build.SOURCES or f.endswith(".cuh")
+                                                      for f in build.HV_SOURCES)
