@@ -286,3 +286,20 @@ def test_autotune_keeps_results(shape, dtype, nvec):
     ms, tried = h.autotune(dtype, nvec, reps=2)
     assert ms > 0 and tried >= 2
     _check(m, h, dtype, nvec, alpha=0.9, beta=0.0, seed=5)
+
+
+def test_last_kernel_names_the_launch():
+    """hphi_last_kernel reports the instance that ran and the source hash the
+    library was built from (what the bench matches profiles against)."""
+    import importlib
+    build = importlib.import_module("paper_2307_13222_gb300.build")
+    m, b, h = pair("SPIN_HALF", 16, 8, 0, heisenberg_terms(square(4, 4), 1.0))
+    x = torch.ones(m.dim, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    hphi.hphi_apply_H(h, x, y)
+    torch.cuda.synchronize()
+    name = h.ctx.last_kernel()
+    assert name.startswith("k_hvp<f32,512,RED0,MINB2>@") and name.endswith("@" + build.source_tag())
+    h.set_tuning(variant=0)
+    hphi.hphi_apply_H(h, x, y)
+    assert h.ctx.last_kernel().startswith("k_hvl<f32,")
