@@ -307,9 +307,11 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
                              (double)ham->D < 4294967296.0;
         const bool spin_staged = (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
                                  ham->model == HPHI_SPIN_HALF && ham->nlo <= 16 && ham->host.n_ll <= 128 && one_col;
-        // Hubbard, one column: the bond-major kernel where its down-hop lists exist
+        // Hubbard, one column: the bond-major kernel where its down-hop lists exist and the
+        // D_dn-row block (x and accumulator) fits in shared memory next to the block set-up
         const bool hub_phased = (ham->tune_variant == 3 || ham->tune_variant < 0) && ham->model == HPHI_HUBBARD &&
-                                ham->ph_ent && one_col;
+                                ham->ph_ent && one_col &&
+                                (double)ham->basis->sp[1].dim * 2.0 * sizeof(T) <= 200.0 * 1024.0;
         const bool staged = spin_staged || hub_phased;
         // spin models: the on-the-fly-rank kernel for unit / pair / 32-wide rows
         int fG = 0, fcpl = 0;

@@ -288,6 +288,15 @@ def test_autotune_keeps_results(shape, dtype, nvec):
     _check(m, h, dtype, nvec, alpha=0.9, beta=0.0, seed=5)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_hubbard_large_down_sector_falls_back(dtype):
+    """D_dn = C(18, 8) = 43,758 down states: the block of one up string does not
+    fit in shared memory, so one-column launches take the generic kernel."""
+    m, b, h = pair("HUBBARD", 18, 1, 8, hubbard_terms(18, chain(18), t=1.0, U=4.0))
+    _check(m, h, dtype, 1, alpha=0.9, beta=0.3, seed=3)
+    assert not h.ctx.last_kernel().startswith("k_hvp")
+
+
 def test_last_kernel_names_the_launch():
     """hphi_last_kernel reports the instance that ran and the source hash the
     library was built from (what the bench matches profiles against)."""
