@@ -142,9 +142,12 @@ inline HvTables make_tables(const hphi_ham *ham, int real_dtype) {
 // Traversal order of the row blocks for a launch whose rows occupy
 // bytes_per_row in L2.  The high-half bits of h are split into "inner" bits,
 // varied first, so that the blocks of one subcube (about half of L2) stay
-// resident while they are processed, and "outer" bits, chosen as an
-// independent set of the high-high bond graph so that as few bonds as
-// possible connect the subcube to other subcubes.  Hubbard keeps natural order.
+// resident while they are processed, and "outer" bits.  Every off-diagonal
+// bond that touches an outer bit sends its target to another subcube, so the
+// outer set is grown greedily by the bit that adds the fewest such bonds (its
+// bonds minus those to bits already outer); outer bits with the most bonds
+// come first in the counter, so that their flips reach the subcube processed
+// just before or after.  Hubbard keeps natural order.
 inline void set_traversal(hphi_ctx *ctx, const hphi_ham *ham, HvTables &P, double bytes_per_row) {
     P.use_perm = 0;
     P.outer_mask = 0;
@@ -162,20 +165,40 @@ inline void set_traversal(hphi_ctx *ctx, const hphi_ham *ham, HvTables &P, doubl
     if (d < 0) d = 0;
     if (d >= nb) return;
     uint32_t adj[32] = {0};
+    int deg[32] = {0};
     for (int k = 0; k < ham->host.n_hh; k++) {
+        if (ham->host.hh[k].cxy == 0.0) continue;
         adj[ham->host.hh[k].i] |= 1u << ham->host.hh[k].j;
         adj[ham->host.hh[k].j] |= 1u << ham->host.hh[k].i;
+        deg[ham->host.hh[k].i]++;
+        deg[ham->host.hh[k].j]++;
     }
+    for (int k = 0; k < ham->host.n_lh; k++)
+        if (ham->host.lh[k].cxy != 0.0) deg[ham->host.lh[k].a]++;
     const int need = nb - d;
     uint32_t outer = 0;
-    for (int b = nb - 1; b >= 0 && __builtin_popcount(outer) < need; b--)
-        if (!(adj[b] & outer)) outer |= 1u << b;
-    for (int b = nb - 1; b >= 0 && __builtin_popcount(outer) < need; b--) outer |= 1u << b;
+    for (int t = 0; t < need; t++) {
+        int best = -1, bc = 1 << 30;
+        for (int b = nb - 1; b >= 0; b--) {
+            if ((outer >> b) & 1) continue;
+            const int c = deg[b] - __builtin_popcount(adj[b] & outer);
+            if (c < bc) {
+                bc = c;
+                best = b;
+            }
+        }
+        outer |= 1u << best;
+    }
     int k = 0;
     for (int b = 0; b < nb; b++)
         if (!((outer >> b) & 1)) P.hperm[k++] = (uint8_t)b;
-    for (int b = 0; b < nb; b++)
-        if ((outer >> b) & 1) P.hperm[k++] = (uint8_t)b;
+    // outer bits with the most bonds lowest in the counter: those flips go to the
+    // subcube processed just before or after
+    int maxd = 0;
+    for (int b = 0; b < nb; b++) maxd = deg[b] > maxd ? deg[b] : maxd;
+    for (int c = maxd; c >= 0; c--)
+        for (int b = 0; b < nb; b++)
+            if (((outer >> b) & 1) && deg[b] == c) P.hperm[k++] = (uint8_t)b;
     P.use_perm = 1;
     P.outer_mask = outer;
 }
