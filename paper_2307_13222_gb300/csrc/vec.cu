@@ -239,6 +239,75 @@ __global__ void __launch_bounds__(kVT) k_lincomb1(int64_t n, const T *x, const T
     if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
 }
 
+// Contiguous rows of nr columns (ld = nr, nr dividing the vector stride): the
+// data is one flat array and a thread's 16-byte vectors always hold the same
+// columns, so the coefficients stay in registers and the column reductions in
+// per-thread accumulators.  Per element the arithmetic of k_lincomb: a x_c,
+// then fma with b x_{c^1} (the pair partner, inside the same vector), then
+// fma with g y_c.  out may alias x or y.
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_lincomb_rows(const LCArgs A) {
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int V = 16 / sizeof(T);
+    __shared__ double sm[kVT][V];
+    const int nr = A.nr;
+    const int64_t tg = blockIdx.x * (int64_t)kVT + threadIdx.x, stride = (int64_t)gridDim.x * kVT;
+    const int c0 = (int)((tg * V) % nr);
+    T ca[V], cb[V], cg[V];
+#pragma unroll
+    for (int e = 0; e < V; e++) {
+        const int c = c0 + e;
+        ca[e] = (T)(A.coef_dev ? A.coef_dev[c] : A.a[c]);
+        cb[e] = (T)(A.coef_dev ? A.coef_dev[nr + c] : A.b[c]);
+        cg[e] = (T)(A.coef_dev ? A.coef_dev[2 * nr + c] : A.g[c]);
+    }
+    const VT *xv = (const VT *)A.x, *yv = (const VT *)A.y;
+    VT *ov = (VT *)A.out;
+    const int64_t nv = A.n * nr / V;
+    Acc<T> s[V];
+    for (int64_t i0 = tg; i0 < nv; i0 += stride * 2) {
+        VT xr[2], yr[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < nv) {
+                xr[u] = xv[i];
+                if (yv) yr[u] = yv[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < nv) {
+                const T *xe = (const T *)&xr[u], *ye = (const T *)&yr[u];
+                VT r;
+                T *re = (T *)&r;
+#pragma unroll
+                for (int e = 0; e < V; e++) {
+                    T v = ca[e] * xe[e];
+                    if (cb[e] != (T)0) v = fma(cb[e], xe[e ^ 1], v);
+                    if (yv && cg[e] != (T)0) v = fma(cg[e], ye[e], v);
+                    re[e] = v;
+                    if (A.red) s[e].add(v, v);
+                }
+                ov[i] = r;
+            }
+        }
+    }
+    if (!A.red) return;
+#pragma unroll
+    for (int e = 0; e < V; e++) sm[threadIdx.x][e] = s[e].value();
+    __syncthreads();
+    for (int c = threadIdx.x; c < nr; c += kVT) {
+        double acc = 0.0;
+        for (int t = 0; t < kVT; t++) {
+            const int ct = (int)(((blockIdx.x * (int64_t)kVT + t) * V) % nr);
+            if (c >= ct && c < ct + V) acc += sm[t][c - ct];
+        }
+        A.partials[(int64_t)blockIdx.x * nr + c] = acc;
+    }
+}
+
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------
 __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
     for (int r = 0; r < 10; r++) {
@@ -485,6 +554,20 @@ int launch_lincomb(hphi_ctx *ctx, LinComb &L) {
         A.a[c] = (c < L.nr && L.a_h) ? L.a_h[c] : 0.0;
         A.b[c] = (c < L.nr && L.b_h) ? L.b_h[c] : 0.0;
         A.g[c] = (c < L.nr && L.g_h) ? L.g_h[c] : 0.0;
+    }
+    // contiguous rows of several columns with 16-byte aligned operands: the flat kernel
+    {
+        const int V = L.real_dtype == HPHI_F64 ? 2 : 4;
+        const int64_t vstride = (int64_t)kVT * V;  // a multiple of the stride of every grid
+        if (L.nr > 1 && L.nr <= 256 && L.nr % V == 0 && vstride % L.nr == 0 && L.ldx == L.nr &&
+            (!L.y || L.ldy == L.nr) && L.ldo == L.nr && al16(L.x) && al16(L.y) && al16(L.out)) {
+            const int slot = prof_begin(ctx, PROF_VEC);
+            if (L.real_dtype == HPHI_F64) k_lincomb_rows<double><<<L.grid, kVT, 0, ctx->stream>>>(A);
+            else k_lincomb_rows<float><<<L.grid, kVT, 0, ctx->stream>>>(A);
+            prof_end(ctx, slot);
+            HPHI_CUDA(ctx, cudaGetLastError());
+            return HPHI_OK;
+        }
     }
     int slot = prof_begin(ctx, PROF_VEC);
     const int cpl = (L.nr + A.tpr - 1) / A.tpr;

@@ -62,3 +62,23 @@ def test_empty_vectors():
     c = ctx()
     x = torch.empty((0, 2), dtype=torch.float64, device="cuda")
     assert (hphi.hphi_dot(c, x, x) == 0).all()
+
+
+@pytest.mark.parametrize("dtype,nvec", [(torch.float32, 4), (torch.float32, 32), (torch.float64, 2),
+                                        (torch.float64, 16), (torch.complex64, 2), (torch.complex64, 16),
+                                        (torch.complex128, 8)])
+def test_axpy_scal_contiguous_rows(dtype, nvec):
+    """Rows of several contiguous columns whose width divides the 16-byte vector
+    stride take the flat kernel (complex scaling uses the pair term in place)."""
+    c = ctx()
+    cplx = dtype.is_complex
+    n = 40001
+    x = torch.from_numpy(random_vectors(n, nvec, 5, complex_=cplx, normalize=False)).to(dtype).cuda()
+    y = torch.from_numpy(random_vectors(n, nvec, 6, complex_=cplx, normalize=False)).to(dtype).cuda()
+    a = (np.arange(nvec) - 1.5) * (0.3 + 0.8j if cplx else 1.0)
+    want = y.cpu().numpy() + a * x.cpu().numpy()
+    hphi.hphi_axpy(c, a, x, y)
+    assert rel_err(y.cpu().numpy(), want) < (1e-15 if dtype in (torch.float64, torch.complex128) else 1e-6)
+    want2 = a * x.cpu().numpy()
+    hphi.hphi_scal(c, a, x)
+    assert rel_err(x.cpu().numpy(), want2) < (1e-15 if dtype in (torch.float64, torch.complex128) else 1e-6)
