@@ -217,7 +217,7 @@ def traffic_for(path, kernel_name):
     return None
 
 
-def measure_e2e(ctx, ham, dim, dtype_name, K):
+def measure_e2e(ctx, ham, dim, dtype_name, K, world=1):
     """H*x through the public API with HOST buffers: one hphi_apply_H_host call
     over a batch of pinned host vectors.  The timed call (wall clock) includes,
     for every vector, its copy to the device, the product and the copy of the
@@ -227,7 +227,14 @@ def measure_e2e(ctx, ham, dim, dtype_name, K):
     from paper_2307_13222_gb300 import hphi
     tdt = torch.float32 if dtype_name == "f32" else torch.float64
     es = 4 if dtype_name == "f32" else 8
-    nb = max(2, min(K, 8))
+    # vectors per call: up to 8, with the pinned buffers of all ranks of the node
+    # (2 x nb vectors each) kept under a quarter of its memory
+    try:
+        host_bytes = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError, AttributeError):
+        host_bytes = 64 << 30
+    fit = int(0.25 * host_bytes / max(world, 1) / (2.0 * es * dim))
+    nb = max(2, min(K, 8, fit))
     xh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     yh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     xd = torch.empty(dim, dtype=tdt, device="cuda")
@@ -294,7 +301,7 @@ def run_native(args):
     main = measure_dtype(ctx, ham, dim, args.dtype, K, W, dist, world)
     ck = clocks.stop()
     kernel_name = ctx.last_kernel()  # the fused H*x kernel of the timed Lanczos steps
-    e2e = measure_e2e(ctx, ham, dim, args.dtype, K) if not args.no_e2e else None
+    e2e = measure_e2e(ctx, ham, dim, args.dtype, K, world) if not args.no_e2e else None
     other = None
     if args.dtype == "f32" and not args.no_fp64:
         other = measure_dtype(ctx, ham, dim, "f64", max(2, K // 4), 1, dist, world)
