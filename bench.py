@@ -200,6 +200,66 @@ def measure_dtype(ctx, ham, dim, dtype_name, K, W, dist, world):
                 vec_launches=vec_n, vec_ms=vec_ms, e0=r["e0"], steps=r["steps"], es=es)
 
 
+def measure_precision(ham, dim, K):
+    """Energy of the FP32-storage path against the FP64 path on the same
+    workload and start vector (untimed): K Lanczos steps plus the ground-state
+    pass in each precision; the Ritz value and the FP64 Rayleigh quotient of
+    the returned vector (the refined energy) of the FP32 run, each relative to
+    the FP64 run's Rayleigh quotient."""
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    out = {}
+    for name, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        v0 = torch.empty(dim, dtype=tdt, device="cuda")
+        hphi.hphi_random_vector(ham.ctx, v0, 2)
+        gs = torch.empty_like(v0)
+        r = hphi.hphi_lanczos(ham, v0, K, 0.0, check_every=K, gs_out=gs)
+        out[name] = (r["e0"], r["e0_rq"])
+        del v0, gs
+        torch.cuda.empty_cache()
+    ref = out["f64"][1]
+    return {"steps": K, "e0_f64_rq": ref, "ritz_rel_err_f32": abs(out["f32"][0] - ref) / abs(ref),
+            "rq_rel_err_f32": abs(out["f32"][1] - ref) / abs(ref), "ritz_rel_err_f64": abs(out["f64"][0] - ref) / abs(ref)}
+
+
+def measure_block_leg(ctx, steps=2, autotune=True):
+    """The cTPQ benchmark's block H*V at its own size: 16 complex FP32 columns
+    over the 2^26 states of the 26-site random 3-regular graph; `steps` TPQ
+    steps (6 Horner stages each) after one warm-up step, the stage kernel timed
+    by the library's CUDA events.  Algorithmic bytes per stage: read V, gather
+    W, write W' = 3 x 8 B per row and complex column."""
+    import numpy as np
+    import torch
+    from paper_2307_13222_gb300 import hphi
+    from workloads import configs
+    cfg = configs.ctpq_random_regular()
+    b = hphi.Basis(ctx, "SPIN_HALF_GC", cfg["n_sites"])
+    h = hphi.Hamiltonian(ctx, b, cfg["terms"])
+    tuned = h.autotune(torch.complex64, cfg["n_vec"], reps=2) if autotune else None
+    V = torch.empty((b.dim, cfg["n_vec"]), dtype=torch.complex64, device="cuda")
+    hphi.hphi_random_vector(ctx, V, cfg["seed"])
+    n2 = np.zeros(cfg["n_vec"])
+    hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(0)
+    for _ in range(steps):
+        hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], n2)
+    n, ms = ctx.profile_read(0)
+    ctx.profile(False)
+    kernel = ctx.last_kernel()
+    del V, h, b
+    torch.cuda.empty_cache()
+    stage_bytes = 3.0 * 8 * cfg["n_vec"] * (1 << cfg["n_sites"])
+    avg = ms / max(n, 1)
+    peak, kind = peaks()
+    ach = stage_bytes / (avg * 1e-3) / 1e9
+    return {"workload": "ctpq_rrg3_N26_B16_c64", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": "of measured" if kind == "measured" else "of fallback",
+            "avg_stage_ms": avg, "stages": n, "bytes_per_stage": stage_bytes, "kernel": kernel,
+            "autotuned_ms": tuned[0] if tuned else None}
+
+
 def traffic_for(path, kernel_name):
     """DRAM bytes per launch from a committed ncu summary, or None unless the
     summary's `kernel:` line names exactly the kernel instance that ran (its
@@ -234,7 +294,10 @@ def measure_e2e(ctx, ham, dim, dtype_name, K, world=1):
     except (ValueError, OSError, AttributeError):
         host_bytes = 64 << 30
     fit = int(0.25 * host_bytes / max(world, 1) / (2.0 * es * dim))
-    nb = max(2, min(K, 8, fit))
+    if fit < 1:
+        return dict(skipped=f"one host vector pair ({2 * es * dim} bytes) exceeds a quarter of the node's memory "
+                            f"shared among {world} ranks")
+    nb = min(max(K, 1), 8, fit)
     xh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     yh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
     xd = torch.empty(dim, dtype=tdt, device="cuda")
@@ -301,10 +364,14 @@ def run_native(args):
     main = measure_dtype(ctx, ham, dim, args.dtype, K, W, dist, world)
     ck = clocks.stop()
     kernel_name = ctx.last_kernel()  # the fused H*x kernel of the timed Lanczos steps
-    e2e = measure_e2e(ctx, ham, dim, args.dtype, K, world) if not args.no_e2e else None
+    # ranks sharing this node's host memory (torchrun sets LOCAL_WORLD_SIZE)
+    node_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+    e2e = measure_e2e(ctx, ham, dim, args.dtype, K, node_ranks) if not args.no_e2e else None
     other = None
     if args.dtype == "f32" and not args.no_fp64:
         other = measure_dtype(ctx, ham, dim, "f64", max(2, K // 4), 1, dist, world)
+    prec = measure_precision(ham, dim, K) if args.dtype == "f32" and not args.no_fp64 else None
+    block = measure_block_leg(ctx, autotune=not args.no_autotune) if not args.no_block else None
     peak, peak_kind = peaks()
     # dominant kernel: the fused H*x of the Lanczos step; algorithmic bytes per
     # launch = gather x + read w_{k-1} + write u = 3 vectors (24 B/row FP64, 12 B/row FP32)
@@ -344,7 +411,9 @@ def run_native(args):
     }
     if ck:
         line["clocks"] = ck
-    if e2e:
+    if e2e and "skipped" in e2e:
+        line["e2e"] = {"value": None, "unit": "GB/s", "skipped": e2e["skipped"]}
+    elif e2e:
         line["e2e"] = {"value": e2e["value"], "unit": "GB/s", "h2d_bytes_per_step": e2e["h2d"],
                        "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"], "step": "hphi_apply_H_host",
                        "vectors_per_call": e2e["batch"], "calls_ms_per_vector": e2e["calls"],
@@ -355,6 +424,10 @@ def run_native(args):
                         "hv_kernel_gbps": a64, "frac": a64 / peak}
     if cpu:
         line["cpu_baseline"] = cpu
+    if prec:
+        line["precision"] = prec
+    if block:
+        line["block"] = block
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.profile(False)
@@ -560,16 +633,22 @@ def run_hubbard4x4(args):
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], check_every=5, reorth=True)
+        gs = torch.empty_like(v0)
+        r = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], check_every=5, reorth=True, gs_out=gs)
         e1.record()
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
         es = 4 if tdt == torch.float32 else 8
         out[dt_name] = dict(ms=ms, r=r, roof=_roofline(ctx, 3.0 * es * b.dim, ctx.last_kernel()))
-        del v0
+        del v0, gs
         torch.cuda.empty_cache()
     ck = clocks.stop()
     f32, f64 = out["f32"], out["f64"]
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", "lanczos_hubbard4x4_U8.json")
+    if os.path.exists(gpath):
+        with open(gpath) as fh:
+            gold = json.load(fh)["e0"]
     es = 4
     line = _base(args, world, "hv_gbps", job_gbps(world, f32["r"]["steps"] * 2.0 * es * b.dim, f32["ms"]), "GB/s",
                  f32["ms"] / max(f32["r"]["steps"], 1), "f32",
@@ -579,6 +658,11 @@ def run_hubbard4x4(args):
     line["steps"] = f32["r"]["steps"]
     line.update({"roofline": f32["roof"], "e0_f32": f32["r"]["e0"], "e0_f64": f64["r"]["e0"],
                  "e0_rel_err_f32": abs(f32["r"]["e0"] - f64["r"]["e0"]) / abs(f64["r"]["e0"]),
+                 "e0_rq_f32": f32["r"]["e0_rq"], "e0_rq_f64": f64["r"]["e0_rq"], "e0_oracle_golden": gold,
+                 "rel_err_vs_oracle": None if gold is None else {
+                     "f32_ritz": abs(f32["r"]["e0"] - gold) / abs(gold),
+                     "f32_rayleigh_fp64": abs(f32["r"]["e0_rq"] - gold) / abs(gold),
+                     "f64_ritz": abs(f64["r"]["e0"] - gold) / abs(gold)},
                  "time_to_solution_s": {"f32": f32["ms"] / 1e3, "f64": f64["ms"] / 1e3},
                  "lanczos_steps": {"f32": f32["r"]["steps"], "f64": f64["r"]["steps"]},
                  "gpu_launches": None})
@@ -632,14 +716,15 @@ def run_ctpq26(args):
     curve = None
     if args.curve:
         # E(T) and C(T) per site from the paper's bootstrap (16 samples, 8 resamplings)
-        (hm, hs), (fm, fs) = hphi.tpq_thermo(np.array(rec_e).T, np.array(rec_h2).T, np.array(rec_ln).T, P=16, M=8)
         betas = cfg["dtau"] * np.arange(args.steps)
+        bs = hphi.hphi_tpq_bootstrap(np.array(rec_e).T, np.array(rec_h2).T, np.array(rec_ln).T, P=16, M=8,
+                                     beta=betas, seed=1)
         curve = []
         for T in (8.0, 4.0, 2.0, 1.0, 0.5, 0.25, 0.1, 0.05, 0.025):
             k = int(round(1.0 / T / cfg["dtau"]))
             if 0 < k < args.steps:
-                curve.append({"T": 1.0 / betas[k], "E_per_site": hm[k] / 26, "E_sd": hs[k] / 26,
-                              "C_per_site": betas[k] ** 2 * fm[k] / 26, "C_sd": betas[k] ** 2 * fs[k] / 26})
+                curve.append({"T": 1.0 / betas[k], "E_per_site": bs["e_mean"][k] / 26, "E_sd": bs["e_sd"][k] / 26,
+                              "C_per_site": bs["c_mean"][k] / 26, "C_sd": bs["c_sd"][k] / 26})
     es = 8 if tdt == torch.complex64 else 16
     # algorithmic bytes of one Horner stage: read V + gather W + write W' per complex column
     stage_bytes = 3.0 * es * cfg["n_vec"] * b.dim
@@ -694,7 +779,7 @@ def run_szz(args):
     qs = 2 * np.pi * np.arange(L // 2 + 1) / L
     z = lz["e0"] + np.linspace(0.0, 4.0, 200) + 0.05j
     tol = 1e-8 if tdt == torch.float64 else 1e-6
-    hphi.hphi_szz_spectrum(h, b, gsd, qs, z, 3000, tol, check_every=10)
+    hphi.hphi_szz_spectrum(h, gsd, qs, z, 3000, tol, check_every=10)
     torch.cuda.synchronize()
     ctx.profile(True)
     ctx.profile_read(0)
@@ -703,13 +788,13 @@ def run_szz(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        Sq, Dq, r = hphi.hphi_szz_spectrum(h, b, gsd, qs, z, 3000, tol, check_every=10)
+        Sq, Dq, r = hphi.hphi_szz_spectrum(h, gsd, qs, z, 3000, tol, check_every=10)
     e1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     es = 4 if tdt == torch.float32 else 8
-    ncol = r["G"].shape[0]
+    ncol = sum(2 if np.abs(np.sin(q * np.arange(L))).max() > 1e-12 else 1 for q in qs)
     line = _base(args, world, "spectra_per_s", world * args.steps / (ms * 1e-3), "spectra/s", ms / args.steps,
                  args.dtype, {"workload": "szz_chain_L24", "dim": b.dim, "q_points": len(qs), "shifts": len(z),
                               "eta": 0.05, "tol": tol, "rhs_columns": ncol, "parallelism": f"replicas{world}",
@@ -891,6 +976,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch settings")
+    ap.add_argument("--no-block", action="store_true", help="skip the cTPQ block H*V leg of the default line")
     ap.add_argument("--curve", action="store_true",
                     help="ctpq26: run from beta = 0 and report E(T), C(T) per site (bootstrap)")
     ap.add_argument("--lattice", default="6x5",

@@ -174,7 +174,12 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         N_lo <= 16), 3 = bond-major: the staged block's H x
  *                         accumulated in shared memory one bond at a time over
  *                         precomputed lists of the rows the bond applies to
- *                         (same shapes as 2; automatic there)
+ *                         (same shapes as 2), 4 = segment: two passes, the
+ *                         high-high and the low-part/high bonds strip by
+ *                         strip of the low half's upper bits (each strip
+ *                         L2-resident), the rest block by block with the
+ *                         targets ranked from shared tables (same shapes as
+ *                         2, at most 32 bonds of each class, D < 2^31)
  *   HPHI_TUNE_COOP        32-column rows: 1-5 = the lanes of a row split the
  *                         bond evaluation and share targets (1: 8 targets per
  *                         batch, registers for 2 thread blocks per SM; 2: 4
@@ -231,13 +236,34 @@ HPHI_API int hphi_apply_H_host(hphi_ctx *ctx, const hphi_ham *ham, int dtype, in
                                const void *x_host, void *y_host, double alpha);
 
 /* ---- matrix pattern (debug; the paper's Matrix Market export, Sec. 3.1.2) --
- * Rows [row0, row1) of H: for each row the distinct columns (ascending) with
- * the summed matrix element, the diagonal always included.  rowptr_host has
- * row1-row0+1 entries; cols_host / vals_host hold at least *nnz_capacity
- * entries.  On HPHI_E_INVAL because the capacity is too small, *nnz_capacity
- * is set to the needed count.  Host outputs; small row ranges only. */
-HPHI_API int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, int64_t *rowptr_host,
-                      int64_t *cols_host, double *vals_host, int64_t *nnz_capacity);
+ * hphi_dump_pattern: the off-diagonal entries of rows [row0, row1) of H, one
+ * entry per term acting on the row's basis state (a HOP with spin = -1 gives
+ * its up entry, then its down entry), ordered by row and then by term id:
+ *   rows_host[k], cols_host[k]  the entry's row and column,
+ *   signs_host[k]  the fermion sign of a hop, (-1)^(# occupied sites of the
+ *                  hopping species strictly between i and j); +1 for a spin
+ *                  flip,
+ *   term_ids_host[k]  the index of the term in the list given to
+ *                  hphi_build_hamiltonian.
+ * The matrix element of the entry is sign * (-t) for a hop and Jxy/2 for a
+ * spin flip (EXCHANGE: Jxy = J); terms with t = 0 or Jxy = 0 give no entry.
+ * Duplicate or cancelling terms stay separate entries.  The diagonal is not
+ * listed.  *count: in, the capacity of the four host arrays; out, the number
+ * of entries.  With too small a capacity (or any array NULL) the call
+ * returns HPHI_E_INVAL and sets *count to the number needed.  At most 2^22
+ * rows per call.  HPHI_E_DEVICE_CHECK if a target falls outside the sector.
+ *
+ * hphi_dump_pattern_merged: the same rows with the entries of equal column
+ * merged (summed), columns ascending, the diagonal always included, in CSR
+ * form: rowptr_host has row1-row0+1 entries; cols_host / vals_host hold at
+ * least *nnz_capacity entries.  On HPHI_E_INVAL because the capacity is too
+ * small, *nnz_capacity is set to the needed count.  This is the matrix the
+ * paper's Matrix Market file lists. */
+HPHI_API int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, int64_t *rows_host,
+                               int64_t *cols_host, int8_t *signs_host, int32_t *term_ids_host, int64_t *count);
+HPHI_API int hphi_dump_pattern_merged(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1,
+                                      int64_t *rowptr_host, int64_t *cols_host, double *vals_host,
+                                      int64_t *nnz_capacity);
 
 /* ---- vector kernels ---------------------------------------------------------
  * n rows, nvec columns, leading dimensions in elements of `dtype`.
@@ -268,23 +294,32 @@ HPHI_API int hphi_random_vector(hphi_ctx *ctx, int dtype, int64_t n, int nvec, u
  * synchronise the device, is not acceptable.  Such callers cannot create an
  * hphi_ctx (its workspace is allocated), so this entry point takes the device
  * and stream directly.
- * It computes exactly what hphi_dot computes (same kernels, same fixed-order
- * reduction) for nvec columns of dtype on `device`, enqueued on `stream`
- * (a cudaStream_t, NULL = legacy default stream), and waits for that stream.
+ * It computes <x_q|y_q> for nvec columns of dtype on `device` with the
+ * kernels of hphi_dot (same per-block partial sums, same fixed-order final
+ * sum), enqueued on `stream` (a cudaStream_t, NULL = legacy default stream),
+ * and waits for that stream.  Its grid is hphi_dot's (at most 8 blocks per
+ * SM) capped at HPHI_DOT_STATIC_MAX_BLOCKS: on devices with at most
+ * HPHI_DOT_STATIC_MAX_BLOCKS / 8 SMs (GB300 has 152) both calls sum in the
+ * same order and return bitwise-equal results; on larger devices the block
+ * partition of long vectors differs and the results agree to rounding.
+ * x and y must be device memory of `device` (or managed memory); anything
+ * else returns HPHI_E_INVAL.
  * Scratch: a file-scope device array of HPHI_DOT_STATIC_SCRATCH_BYTES
- * (about 0.5 MB) that every GPU which loads the library keeps until the
+ * (about 2 MB) that every GPU which loads the library keeps until the
  * process exits; no cudaMalloc, cudaFree or allocating library routine is
- * called.  Limits: at most HPHI_DOT_STATIC_MAX_REAL real columns (a complex
- * column counts two); larger requests return HPHI_E_INVAL.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  The
- * calling thread's current device is restored before returning.
+ * called.  Every call looks up the array's device address with `device`
+ * current (a host-side lookup that allocates nothing).  The first call on a
+ * device may also load the library's device code onto it, so make that
+ * first call before any stream capture.  Limits: at most
+ * HPHI_DOT_STATIC_MAX_REAL real columns (a complex column counts two);
+ * larger requests return HPHI_E_INVAL.  The calling thread's current device
+ * is restored before returning.
  * Every call uses the same array, and nothing in it needs to start at zero
  * (each call writes every slot it reads before reading it).  Calls that
  * overlap on the GPU (other streams, other threads) race on the array: do not
  * overlap them. */
 #define HPHI_DOT_STATIC_MAX_REAL 64
-#define HPHI_DOT_STATIC_MAX_BLOCKS 512
+#define HPHI_DOT_STATIC_MAX_BLOCKS 2048
 #define HPHI_DOT_STATIC_SCRATCH_BYTES (8 * (2 * HPHI_DOT_STATIC_MAX_BLOCKS * HPHI_DOT_STATIC_MAX_REAL + 2 * HPHI_DOT_STATIC_MAX_REAL))
 HPHI_API int hphi_dot_static(int device, void *stream, int dtype, int64_t n, int nvec, const void *x, int64_t ldx,
                              const void *y, int64_t ldy, double *out_host);
@@ -316,7 +351,13 @@ typedef struct hphi_lanczos_result {
     double resid_est; /* beta_{m+1} |y_m| */
     double resid;     /* |H x - e0 x| (only with gs_out), else -1 */
     int steps;
-    int breakdown; /* 1 if an invariant subspace ended the run */
+    int breakdown;    /* 1 if an invariant subspace ended the run */
+    double e0_rq;     /* <x|H x> / <x|x> of the returned ground-state vector x
+                         in FP64 arithmetic (an FP32 x is widened first), only
+                         with gs_out, else NaN; NaN also when the two FP64
+                         work vectors it needs (one for F64) cannot be
+                         allocated.  For F32 storage this is the refined
+                         energy: its error is quadratic in the error of x */
 } hphi_lanczos_result;
 
 HPHI_API int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos_opts *opts, const void *v0, void *gs_out,
@@ -496,6 +537,26 @@ HPHI_API int hphi_shifted_krylov(hphi_ctx *ctx, const hphi_ham *ham, const hphi_
                                  double *resid_host, double *alpha_host, double *beta_host,
                                  hphi_krylov_result *result);
 
+/* hphi_szz_spectrum: the spin structure factor of Sec. 3.2 for nq wave
+ * numbers at once,
+ *   D_q(z_j) = <Phi_q| (z_j I - H)^{-1} |Phi_q>,  Phi_q = sum_l e^{i q l} S^z_l Phi_0,
+ *   S^zz(q, z_j) = -Im D_q(z_j),
+ * with Phi_0 = gs (device, D elements of opts->dtype, F64 or F32, contiguous)
+ * and the shifts z_j = z_host[2j] + i z_host[2j+1] (the caller adds E_0:
+ * z = E_0 + omega + i eta).  Each Phi_q = a + i b is split into real columns
+ * a and b (b is left out when sin(q l) vanishes for every site, |sin| <=
+ * 1e-12), all columns share one hphi_shifted_krylov run (same opts, same
+ * stopping rule), and D_q = D_a + D_b ((z - H)^{-1} is complex symmetric).
+ * Host outputs: s_host[q nz + j] = S^zz; d_host (nullable) [q nz + j] as
+ * (re, im) pairs; resid_host (nullable) [q nz + j] the larger relative
+ * residual of the two columns; *result as hphi_shifted_krylov.
+ * Limits: the columns (one or two per q) must number at most 64.  The
+ * library allocates the excitation block (D x (columns + 1) elements) for the
+ * call.  Returns HPHI_OK, HPHI_E_NOTCONV (outputs filled in) or an error. */
+HPHI_API int hphi_szz_spectrum(hphi_ctx *ctx, const hphi_ham *ham, const hphi_krylov_opts *opts, const void *gs,
+                               int nq, const double *q_host, int nz, const double *z_host, double *s_host,
+                               double *d_host, double *resid_host, hphi_krylov_result *result);
+
 /* ---- LOBPCG (Sec. 3.3) -------------------------------------------------------------
  * hphi_lobpcg: the m lowest eigenpairs (1 <= m <= 32) of H by the locally
  * optimal block conjugate gradient method (no preconditioner): each
@@ -512,13 +573,41 @@ HPHI_API int hphi_lobpcg(hphi_ctx *ctx, const hphi_ham *ham, int m, void *X, int
 
 /* ---- microcanonical TPQ step (Sec. 3.5.1) ---------------------------------------
  * Phi_{k+1} = U_m Phi_k, U_m = 1 - (dtau/2) H with dtau = 2 / (l n_sites): the
- * cTPQ step above with nmax = 1 (same arguments, layout and outputs).  The
- * inverse temperature of the state the step starts from is
- * beta_k = k dtau / (1 - u_k / l), u_k = e_host[q] / n_sites; l must exceed
- * the largest eigenvalue of H / n_sites for U_m to be positive on the spectrum.
- * HPHI_E_INVAL for l <= 0 or n_sites < 1. */
+ * cTPQ step above with nmax = 1 (same arguments, layout and outputs).  k is
+ * the step index of the state the step starts from (Phi_0 = the random
+ * start vector); beta_host (nullable, host, nvec) receives its inverse
+ * temperature beta_k = k dtau / (1 - u_k / l), u_k = e_host[q] / n_sites.
+ * l must exceed the largest eigenvalue of H / n_sites for U_m to be positive
+ * on the spectrum.  HPHI_E_INVAL for l <= 0, n_sites < 1 or k < 0. */
 HPHI_API int hphi_mtpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv, double l,
-                            int n_sites, double *norm2_inout, double *e_host, double *h2_host, double *logd_host);
+                            int n_sites, int k, double *norm2_inout, double *e_host, double *h2_host,
+                            double *logd_host, double *beta_host);
+
+/* ---- thermodynamics of TPQ samples: the bootstrap (Sec. 3.5.1) --------------------
+ * From n_samples independent TPQ runs recorded at n_temps inverse
+ * temperatures beta_k (host arrays, row-major [n_samples][n_temps]):
+ *   e[n][k]  = <Phi|H|Phi> / <Phi|Phi> of sample n at beta_k,
+ *   h2[n][k] = <Phi|H^2|Phi> / <Phi|Phi>,
+ *   log_norm[n][k] = log <Phi|Phi> (any constant per k may be added: norms
+ *            are taken relative to sample 0's, the paper's W(beta_k)),
+ * M resamplings R_m of P sample indices each, drawn with replacement, give
+ *   <A>_m = sum_{p} w_{R_m(p)} A_{R_m(p)} / sum_{p} w_{R_m(p)},
+ *   w_n = exp(log_norm[n][k] - log_norm[0][k]),
+ * and the outputs (host, n_temps each) are the mean over m and the standard
+ * deviation sigma^2 = 1/(M-1) sum_m (x_m - mean)^2 (0 for M = 1) of
+ *   E_m = <H>_m                         -> e_mean, e_sd
+ *   C_m = beta_k^2 (<H^2>_m - <H>_m^2)  -> c_mean, c_sd (nullable pair; with
+ *         beta NULL the factor beta_k^2 is left out).
+ * picks (nullable, host, [M][P]) are the resamplings; with picks NULL they
+ * are drawn from Philox4x32-10: pick e = m P + p is floor(U n_samples)
+ * (at most n_samples - 1), U = (((w1 << 32) | w0) >> 11 + 0.5) 2^-53 of
+ * output words w0, w1 for counter (e mod 2^32, e div 2^32, 0, 0) and key
+ * (seed mod 2^32, seed div 2^32).  Host only; no GPU needed.
+ * Errors: HPHI_E_INVAL (sizes < 1, a NULL input, a pick out of range),
+ * HPHI_E_NUMERIC (non-finite weights or a zero weight sum). */
+HPHI_API int hphi_tpq_bootstrap(int n_samples, int n_temps, const double *e, const double *h2,
+                                const double *log_norm, const double *beta, int P, int M, const int32_t *picks,
+                                uint64_t seed, double *e_mean, double *e_sd, double *c_mean, double *c_sd);
 
 /* ---- host utility: symmetric tridiagonal eigenproblem ------------------------
  * All eigenvalues (ascending) of the n x n tridiagonal with diagonal a[0..n-1]

@@ -381,9 +381,13 @@ static double hop_sign(uint64_t s, int i, int j)
 
 /* All matrix elements H[r][col] of row r, in term order: entry 0 is the
  * diagonal (sum of the diagonal parts of every term, term id -1); each
- * off-diagonal entry comes from one term acting on the row's state.  Returns
+ * off-diagonal entry comes from one term acting on the row's state (a HOP on
+ * both species gives its up entry, then its down entry).  signs (nullable)
+ * receives the fermion sign of each entry: (-1)^(# occupied sites strictly
+ * between i and j) for a hop, +1 for spin flips and the diagonal.  Returns
  * the count, or a negative status (a target outside the sector is an error). */
-int orc_row_entries(const orc_model *m, int64_t r, int64_t *cols, double *vals, int32_t *tids, int cap)
+int orc_row_entries(const orc_model *m, int64_t r, int64_t *cols, double *vals, int32_t *tids, int8_t *signs,
+                    int cap)
 {
     uint64_t su, sd;
     orc_row_state(m, r, &su, &sd);
@@ -410,6 +414,8 @@ int orc_row_entries(const orc_model *m, int64_t r, int64_t *cols, double *vals, 
                 cols[cnt] = c;
                 vals[cnt] = 0.5 * Jxy;
                 tids[cnt] = k;
+                if (signs)
+                    signs[cnt] = 1;
                 cnt++;
             }
         } else if (t->kind == ORC_HOP) {
@@ -426,9 +432,12 @@ int orc_row_entries(const orc_model *m, int64_t r, int64_t *cols, double *vals, 
                     return ORC_EINVAL;
                 if (cnt >= cap)
                     return ORC_EINVAL;
+                double sg = hop_sign(s, i, j);
                 cols[cnt] = c;
-                vals[cnt] = -t->v0 * hop_sign(s, i, j);
+                vals[cnt] = -t->v0 * sg;
                 tids[cnt] = k;
+                if (signs)
+                    signs[cnt] = sg < 0.0 ? -1 : 1;
                 cnt++;
             }
         } else if (t->kind == ORC_HUBBARD_U) {
@@ -440,6 +449,8 @@ int orc_row_entries(const orc_model *m, int64_t r, int64_t *cols, double *vals, 
     cols[0] = r;
     vals[0] = diag;
     tids[0] = -1;
+    if (signs)
+        signs[0] = 1;
     return cnt;
 }
 
@@ -465,7 +476,7 @@ int64_t orc_pattern(const orc_model *m, int64_t r0, int64_t r1, int64_t *rowptr,
     int64_t pos = 0;
     for (int64_t r = r0; r < r1; r++) {
         rowptr[r - r0] = pos;
-        int n = orc_row_entries(m, r, c, v, t, mx);
+        int n = orc_row_entries(m, r, c, v, t, NULL, mx);
         if (n < 0) {
             pos = n;
             break;
@@ -527,7 +538,7 @@ int orc_apply(const orc_model *m, int nvec, const double *x, int64_t ldx, double
         } else {
 #pragma omp for schedule(static)
             for (int64_t r = r0; r < r1; r++) {
-                int n = orc_row_entries(m, r, c, v, t, mx);
+                int n = orc_row_entries(m, r, c, v, t, NULL, mx);
                 if (n < 0) {
 #pragma omp atomic write
                     bad = 1;

@@ -65,7 +65,7 @@ def _L():
             "orc_model_dim": (i64, [vp]),
             "orc_row_state": (None, [vp, i64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
             "orc_state_row": (i64, [vp, C.c_uint64, C.c_uint64]),
-            "orc_row_entries": (i32, [vp, i64, vp, vp, vp, i32]),
+            "orc_row_entries": (i32, [vp, i64, vp, vp, vp, vp, i32]),
             "orc_max_row_entries": (i32, [vp]),
             "orc_pattern": (i64, [vp, i64, i64, vp, vp, vp, i64]),
             "orc_apply": (i32, [vp, i32, vp, i64, vp, i64, dbl, dbl, i64, i64]),
@@ -176,15 +176,34 @@ class Model:
     def state_row(self, su: int, sd: int = 0) -> int:
         return int(_L().orc_state_row(self._h, int(su), int(sd)))
 
-    def row_entries(self, r: int):
+    def row_entries(self, r: int, with_signs: bool = False):
+        """Row r's entries in term order (diagonal first, term id -1): columns,
+        values, term ids and, with with_signs, the fermion sign of each."""
         mx = _L().orc_max_row_entries(self._h)
         cols = np.zeros(mx, np.int64)
         vals = np.zeros(mx, np.float64)
         tids = np.zeros(mx, np.int32)
-        n = _L().orc_row_entries(self._h, int(r), _ptr(cols), _ptr(vals), _ptr(tids), mx)
+        signs = np.zeros(mx, np.int8)
+        n = _L().orc_row_entries(self._h, int(r), _ptr(cols), _ptr(vals), _ptr(tids), _ptr(signs), mx)
         if n < 0:
             raise ValueError("row entries failed")
+        if with_signs:
+            return cols[:n], vals[:n], tids[:n], signs[:n]
         return cols[:n], vals[:n], tids[:n]
+
+    def pattern_terms(self, r0: int, r1: int):
+        """The unmerged off-diagonal pattern of rows [r0, r1) ordered by (row,
+        term order): arrays rows, cols, signs, term_ids (Sec. 3.1.2 lists H
+        entry by entry; here every term's entry is kept separately)."""
+        rows, cols, signs, tids = [], [], [], []
+        for r in range(r0, r1):
+            c, _, t, sg = self.row_entries(r, with_signs=True)
+            rows.append(np.full(len(c) - 1, r, np.int64))
+            cols.append(c[1:])
+            signs.append(sg[1:])
+            tids.append(t[1:])
+        cat = (lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt))
+        return cat(rows, np.int64), cat(cols, np.int64), cat(signs, np.int8), cat(tids, np.int32)
 
     def pattern(self, r0: int = 0, r1: int | None = None):
         """Merged, column-sorted CSR pattern of rows [r0, r1)."""
@@ -295,13 +314,16 @@ def canonical_thermo(evals: np.ndarray, temps: np.ndarray):
     return np.array(E), np.array(Cv)
 
 
-def bootstrap_tpq(num_h: np.ndarray, num_h2: np.ndarray, log_norm: np.ndarray, P: int, M: int, seed: int):
+def bootstrap_tpq(num_h: np.ndarray, num_h2: np.ndarray, log_norm: np.ndarray, P: int, M: int,
+                  seed: int | None = None, picks: np.ndarray | None = None):
     """The paper's bootstrap over N TPQ samples (Sec. 3.5.1).
 
     Inputs per sample n and temperature index k: the unnormalised expectation
     pieces are num_h[n,k] = <Phi|H|Phi>/<Phi|Phi>, num_h2 likewise for H^2, and
-    log_norm[n,k] = log <Phi^n(beta_k)|Phi^n(beta_k)>.  For m = 0..M-1, P
-    samples R_m(p) are drawn with replacement;
+    log_norm[n,k] = log <Phi^n(beta_k)|Phi^n(beta_k)>.  For m = 0..M-1 the
+    resampling R_m is a list of P sample indices drawn with replacement
+    (picks[m][p]; the random draw is an input: picks, or the seeded Philox
+    stream of workloads.rng.bootstrap_picks when only seed is given);
         A_m = sum_p <Phi^R|A|Phi^R>,  Z_m = sum_p <Phi^R|Phi^R>,  <A>_m = A_m / Z_m,
     with all norms divided by W(beta_k) = <Phi^0|Phi^0> (the paper's
     normalisation by sample 0).  Returns mean and standard deviation over m of
@@ -311,8 +333,11 @@ def bootstrap_tpq(num_h: np.ndarray, num_h2: np.ndarray, log_norm: np.ndarray, P
     """
     num_h = np.asarray(num_h)
     Nn, K = num_h.shape
-    rng = np.random.default_rng(seed)
-    picks = rng.integers(0, Nn, size=(M, P))
+    if picks is None:
+        from workloads.rng import bootstrap_picks
+        picks = bootstrap_picks(M, P, Nn, seed)
+    picks = np.asarray(picks, dtype=np.int64)
+    assert picks.shape == (M, P) and picks.min() >= 0 and picks.max() < Nn
     w = np.exp(log_norm - log_norm[0:1, :])  # tilde norms relative to sample 0
     eh, eh2 = np.zeros((M, K)), np.zeros((M, K))
     for m in range(M):

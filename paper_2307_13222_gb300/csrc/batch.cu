@@ -677,6 +677,7 @@ extern "C" int hphi_lanczos_batch(hphi_ctx *ctx, int nprob, hphi_ham *const *ham
     for (int p = 0; p < nprob; p++) {
         results[p].e0 = theta[p];
         results[p].resid_est = rest[p];
+        results[p].e0_rq = std::nan("");
         results[p].resid = gres[p];
         results[p].steps = mstop[p];
         results[p].breakdown = brk[p];

@@ -191,6 +191,7 @@ extern "C" void hphi_ctx_destroy(hphi_ctx *ctx) {
     for (auto e : ctx->io_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(ctx->dflag);
+    cudaFree(ctx->seg_tmp);
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);

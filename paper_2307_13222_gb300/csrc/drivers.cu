@@ -310,6 +310,66 @@ extern "C" int hphi_tridiag_eigen(int n, const double *a, const double *b, doubl
     return HPHI_OK;
 }
 
+// x (FP32) -> w (FP64), exact
+__global__ void k_widen(int64_t n, const float *__restrict__ x, double *__restrict__ w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = (double)x[i];
+}
+
+// Rayleigh quotient <x|H x> / <x|x> of a device vector in FP64 arithmetic.
+// An FP32 vector is widened to FP64 first, so the product and both
+// reductions run in double precision: for the ground-state vector of an
+// FP32-storage Lanczos run this is the FP64 refinement of the energy (its
+// error is quadratic in the vector's error, where the Ritz value of the FP32
+// recurrence carries the FP32 rounding of alpha and beta linearly).
+// Buffers (D doubles, two for FP32 input) are allocated for the call; when
+// they do not fit, *rq is NaN and the call still succeeds.
+static int rayleigh_fp64(hphi_ctx *ctx, const hphi_ham *ham, int dt, const void *x, double *rq) {
+    *rq = std::nan("");
+    const int64_t D = ham->D;
+    double *buf = nullptr;
+    const size_t nd = (dt == HPHI_F64 ? 1 : 2) * (size_t)D;
+    if (cudaMalloc((void **)&buf, nd * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return HPHI_OK;
+    }
+    const double *x64 = (const double *)x;
+    if (dt == HPHI_F32) {
+        double *w = buf + D;
+        const int64_t g = (D + 255) / 256 < (int64_t)ctx->sm_count * 16 ? (D + 255) / 256 : (int64_t)ctx->sm_count * 16;
+        k_widen<<<(int)(g < 1 ? 1 : g), 256, 0, ctx->stream>>>(D, (const float *)x, w);
+        x64 = w;
+    }
+    int st = ensure_partials(ctx, hv_partials_size(ctx, ham, 1));
+    double *red = ctx->dscal + 3016;
+    if (!st) {
+        HvLaunch R{};
+        R.dtype_real = HPHI_F64;
+        R.ncol = 1;
+        R.x = x64;
+        R.ldx = 1;
+        R.y = buf;
+        R.ldy = 1;
+        R.alpha_s = 1.0;
+        R.red[0] = R_XHX;
+        R.red[1] = R_HXHX;
+        R.red[2] = R_XX;
+        R.partials = ctx->partials;
+        st = launch_hv(ctx, ham, R);
+        if (!st) st = reduce_hv(ctx, R, red);
+    }
+    double r[3] = {0.0, 0.0, 0.0};
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(r, red, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_err(ctx, e, "Rayleigh quotient");
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (!st && r[2] > 0.0) *rq = r[0] / r[2];
+    return st;
+}
+
 // Lanczos with full reorthogonalisation: every normalised Krylov vector is kept
 // and each new direction is projected out of all of them twice (classical
 // Gram-Schmidt, twice is enough), with FP64 projection coefficients.
@@ -484,7 +544,9 @@ static int lanczos_reorth(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lanczos
         HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         res->resid = sqrt(rr);
     }
-    fail(HPHI_OK);
+    fail(HPHI_OK);  // frees the stored Krylov vectors
+    res->e0_rq = std::nan("");
+    if (gs_out && (st = rayleigh_fp64(ctx, ham, dt, gs_out, &res->e0_rq))) return st;
     if (opts->tol > 0.0 && !conv && !brk)
         return set_err(ctx, HPHI_E_NOTCONV, "Lanczos: tolerance not reached in %d steps", m);
     return HPHI_OK;
@@ -721,22 +783,29 @@ extern "C" int hphi_lanczos(hphi_ctx *ctx, const hphi_ham *ham, const hphi_lancz
     }
     HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(ab);
+    res->e0_rq = std::nan("");
+    if (gs_out && (st = rayleigh_fp64(ctx, ham, dt, gs_out, &res->e0_rq))) return st;
     if (opts->tol > 0.0 && !conv && !brk)
         return set_err(ctx, HPHI_E_NOTCONV, "Lanczos: tolerance not reached in %d steps", m);
     return HPHI_OK;
 }
 
 // Microcanonical TPQ (Sec. 3.5.1): U_m = 1 - (dtau / 2) H with dtau = 2 / (l N_s),
-// i.e. the cTPQ step with nmax = 1; the caller forms beta_k = k dtau / (1 - u_k / l)
-// from u_k = e / N_s of the state the step starts from.
+// i.e. the cTPQ step with nmax = 1, plus beta_k = k dtau / (1 - u_k / l) from
+// u_k = e / N_s of the state the step starts from.
 extern "C" int hphi_mtpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv,
-                              double l, int n_sites, double *norm2_inout, double *e_out, double *h2_out,
-                              double *logd_out) {
+                              double l, int n_sites, int k, double *norm2_inout, double *e_out, double *h2_out,
+                              double *logd_out, double *beta_out) {
     if (!ctx || !ham) return HPHI_E_INVAL;
-    if (!(l > 0.0) || !isfinite(l) || n_sites < 1)
-        return set_err(ctx, HPHI_E_INVAL, "mTPQ needs l > 0 and n_sites >= 1");
-    return hphi_tpq_step(ctx, ham, dtype, nvec, V, ldv, 2.0 / (l * (double)n_sites), 1, norm2_inout, e_out, h2_out,
-                         logd_out);
+    if (!(l > 0.0) || !isfinite(l) || n_sites < 1 || k < 0)
+        return set_err(ctx, HPHI_E_INVAL, "mTPQ needs l > 0, n_sites >= 1 and k >= 0");
+    const double dtau = 2.0 / (l * (double)n_sites);
+    const int st = hphi_tpq_step(ctx, ham, dtype, nvec, V, ldv, dtau, 1, norm2_inout, e_out, h2_out, logd_out);
+    if (st == HPHI_OK && beta_out) {
+        // beta_k = k dtau / (1 - u_k / l), u_k the energy per site of Phi_k (Sec. 3.5.1)
+        for (int q = 0; q < nvec; q++) beta_out[q] = (double)k * dtau / (1.0 - e_out[q] / (double)n_sites / l);
+    }
+    return st;
 }
 
 extern "C" int hphi_tpq_step(hphi_ctx *ctx, const hphi_ham *ham, int dtype, int nvec, void *V, int64_t ldv,

@@ -143,6 +143,10 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->ph_off);
     cudaFree(h->dterms_d);
     cudaFree(h->rowstate);
+    cudaFree(h->seg_r8);
+    cudaFree(h->seg_un);
+    cudaFree(h->seg_so);
+    delete h->seg;
     delete h;
 }
 
@@ -305,7 +309,8 @@ int build_spin(hphi_ctx *ctx, hphi_ham *H, const hphi_term *terms, int n_terms) 
     cudaFree(d_ll);
     cudaFree(d_lb);
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_spin_tables");
-    if (sector && nlo <= 16 && ll.size() <= 128) return build_bond_lists(ctx, H, ll, lowbits);
+    if (sector && nlo <= 16 && ll.size() <= 128 && (st = build_bond_lists(ctx, H, ll, lowbits))) return st;
+    if (sector && (st = build_seg_tables(ctx, H))) return st;
     return HPHI_OK;
 }
 
@@ -469,6 +474,7 @@ extern "C" int hphi_build_hamiltonian(hphi_ctx *ctx, const hphi_basis *basis, co
     H->device = ctx->device;
     H->D = basis->D;
     int st = basis->model == HPHI_HUBBARD ? build_hubbard(ctx, H, terms, n_terms) : build_spin(ctx, H, terms, n_terms);
+    if (!st && n_terms > 0) H->terms.assign(terms, terms + n_terms);
     if (!st) {
         st = dev_alloc(ctx, &H->desc, 1);
         if (!st) {

@@ -89,6 +89,25 @@ struct HamDesc {
     double coef[kMaxCoef];
 };
 
+// Segment H*x kernel (hv_seg.cu): bond classes by where the two sites lie
+// (l0 = the lowest min(8, N_lo) bits of the low half, l1 = the rest of it,
+// h = the high half), the n0-bit rank tables and the segment offsets SO.
+constexpr int kSegMax = 32;  // bonds per class
+struct SegArgs {
+    int n0, n1, nlo, nhi, n;
+    int nA, nB, nC, nE, nF;
+    uint8_t A0[kSegMax], A1[kSegMax];  // A: l0 bits i < j
+    uint8_t B0[kSegMax], B1[kSegMax];  // B: l0 bit i, l1 bit b
+    uint8_t C0[kSegMax], C1[kSegMax];  // C: l1 bits
+    uint8_t E0[kSegMax], E1[kSegMax];  // E: l0 bit i, h bit a
+    uint8_t F0[kSegMax], F1[kSegMax];  // F: l1 bit b, h bit a
+    double cA[kSegMax], cB[kSegMax], cC[kSegMax], cE[kSegMax], cF[kSegMax];  // Jxy / 2
+    uint16_t off8[10];  // first position of each popcount class in un8
+    const uint8_t *r8;  // [2^n0] rank of an n0-bit string within its popcount class
+    const uint8_t *un8; // [2^n0] the n0-bit strings ordered by (popcount, value)
+    const uint16_t *so; // [(N_lo + 1) << n1] SO[p][l1]
+};
+
 // Lin tables of one species (spin string, or up / down fermion string).
 struct Species {
     int N = 0, n = 0, nlo = 0, nhi = 0;
@@ -120,6 +139,9 @@ struct hphi_ctx {
     void *vec[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t vec_bytes = 0;
     int *dflag = nullptr;        // device status word of consistency checks
+    // segment H*x: the first pass's partial products when y cannot hold them
+    void *seg_tmp = nullptr;
+    size_t seg_tmp_bytes = 0;
     // streaming H*x on host vectors: two x and two y device buffers, copy
     // streams (host to device, device to host) and their ordering events
     void *io[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -173,9 +195,15 @@ struct hphi_ham {
     int32_t *ph_off = nullptr;
     int64_t ph_mx0 = 0;          // first offset row of the mixed-bond groups
     int max_row_entries = 0;
+    // segment kernel (spin S^z sector, N_lo <= 16): host copy of its
+    // arguments (null when not available) and its device tables
+    hphi::SegArgs *seg = nullptr;
+    uint8_t *seg_r8 = nullptr, *seg_un = nullptr;
+    uint16_t *seg_so = nullptr;
     // plain term list (host and device) and, for the S^z sector, the state of
     // every row (built on first use by the small-problem solver)
     std::vector<hphi::DTerm> dterms;
+    std::vector<hphi_term> terms;  // the interaction list as given (term ids of the pattern export)
     hphi::DTerm *dterms_d = nullptr;
     uint32_t *rowstate = nullptr;
     // launch tuning (hphi_ham_set_tuning)
@@ -279,6 +307,9 @@ int tridiag_ql(int n, double *d, double *e, double *z);
 int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, double *ylast);
 // the same with a warm start (an upper bound of the lowest eigenvalue, updated)
 int lowest_ritz_warm(int m, const double *alpha, const double *beta2, double *warm, double *theta, double *ylast);
+
+// ---- segment H*x tables (hv_seg.cu) -------------------------------------------------
+int build_seg_tables(hphi_ctx *ctx, hphi_ham *H);
 
 // ---- pattern (pattern.cu) --------------------------------------------------------
 int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,

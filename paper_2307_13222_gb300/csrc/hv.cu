@@ -305,14 +305,17 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         // (measured faster than the table-driven kernel on the 6x5 and 4x8 sectors)
         const bool one_col = same_ld && red_mode >= 0 && L.ldx == 1 && L.ncol == 1 && !L.swap &&
                              (double)ham->D < 4294967296.0;
-        const bool spin_staged = (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
+        // the segment kernel (variant 4): spin sector, one column, rows addressed with 32-bit offsets
+        const bool seg = ham->tune_variant == 4 && ham->seg && one_col && (double)ham->D < 2147483648.0;
+        const bool spin_staged = !seg &&
+                                 (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
                                  ham->model == HPHI_SPIN_HALF && ham->nlo <= 16 && ham->host.n_ll <= 128 && one_col;
         // Hubbard, one column: the bond-major kernel where its down-hop lists exist and the
         // D_dn-row block (x and accumulator) fits in shared memory next to the block set-up
         const bool hub_phased = (ham->tune_variant == 3 || ham->tune_variant < 0) && ham->model == HPHI_HUBBARD &&
                                 ham->ph_ent && one_col &&
                                 (double)ham->basis->sp[1].dim * 2.0 * sizeof(T) <= 200.0 * 1024.0;
-        const bool staged = spin_staged || hub_phased;
+        const bool staged = spin_staged || hub_phased || seg;
         // spin models: the on-the-fly-rank kernel for unit / pair / 32-wide rows
         int fG = 0, fcpl = 0;
         // variant -1 (automatic): on-the-fly ranks for 32-wide rows, lists for unit / pair rows
@@ -383,8 +386,9 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
             // the staged kernel on the 6x5 and 4x8 sectors, FP32 and FP64)
             const bool phased = hub_phased || ham->tune_variant == 3 ||
                                 (ham->tune_variant < 0 && ham->ph_ent && ham->host.n_ll <= 128);
-            st = phased ? launch_phased<T>(ctx, ham, a, red_mode, &grid)
-                        : launch_staged<T>(ctx, ham, a, red_mode, &grid);
+            st = seg ? launch_seg<T>(ctx, ham, a, red_mode, &grid)
+                     : phased ? launch_phased<T>(ctx, ham, a, red_mode, &grid)
+                              : launch_staged<T>(ctx, ham, a, red_mode, &grid);
         } else if (fG) {
             set_traversal(ctx, ham, a.P, (double)nc * sizeof(T) < 4.0 ? 4.0 : (double)nc * sizeof(T));
             a.P.split = ham->tune_split;
@@ -473,7 +477,7 @@ extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
         ham->tune_hints = value;
         return HPHI_OK;
     case HPHI_TUNE_VARIANT:
-        if (value < -1 || value > 3) return HPHI_E_INVAL;
+        if (value < -1 || value > 4) return HPHI_E_INVAL;
         ham->tune_variant = value;
         return HPHI_OK;
     case HPHI_TUNE_COOP:

@@ -217,5 +217,8 @@ int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int re
 template <typename T>
 int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
 uint32_t staged_block_len(const hphi_ham *ham);
+// segment kernel (hv_seg.cu): spin sector, one column, two passes
+template <typename T>
+int launch_seg(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, int red_mode, int *grid);
 
 }  // namespace hphi

@@ -1,6 +1,13 @@
-// Debug export of the matrix pattern (the paper's Matrix Market output of H,
-// Sec. 3.1.2): rows [row0, row1) enumerated by the same row visitor as the
-// H*x kernel, then sorted and merged per row on the host.
+// Debug exports of the matrix pattern (the paper's Matrix Market output of H,
+// Sec. 3.1.2).
+//   hphi_dump_pattern: every off-diagonal entry of rows [row0, row1) as
+//     (row, col, fermion sign, term id), one entry per term (and species)
+//     acting on the row's state, in term order: the row's state from the
+//     basis (Lin-table unrank), the target's row from the basis rank (Lin's
+//     two tables), the sign from the popcount of the occupied sites between
+//     the hop's ends.  Duplicate and cancelling terms stay separate entries.
+//   hphi_dump_pattern_merged: rows enumerated by the same row visitor as the
+//     H*x kernel, then sorted and merged per row on the host.
 #include <algorithm>
 #include <vector>
 
@@ -79,6 +86,90 @@ HvTables tables_f64(const hphi_ham *ham) {
     return P;
 }
 
+// ---- term-order export ---------------------------------------------------------
+struct TermSp {             // Lin tables and unrank data of one species
+    const uint32_t *ja;
+    const uint64_t *jb, *jbp;
+    const uint32_t *loff, *lstate;
+    int N, n, nlo, nhi;
+};
+
+__device__ __forceinline__ int64_t tsp_rank(const TermSp &s, uint64_t x) {
+    if (s.N < 64 && (x >> s.N) != 0) return -1;
+    if (__popcll(x) != s.n) return -1;
+    const uint64_t b = s.jb[x >> s.nlo];
+    if (b == ~0ull) return -1;
+    return (int64_t)(b + s.ja[x & ((1ull << s.nlo) - 1)]);
+}
+
+__device__ __forceinline__ uint64_t tsp_state(const TermSp &s, uint64_t r) {
+    uint64_t lo = 0, hi = 1ull << s.nhi;  // largest h with jbp[h] <= r
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (s.jbp[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    const int p = s.n - __popcll(lo);
+    return (lo << s.nlo) | s.lstate[s.loff[p] + (uint32_t)(r - s.jbp[lo])];
+}
+
+// One thread per row: the row's off-diagonal entries in term order.  stride
+// = 2 n_terms slots per row (a hop on both species gives two entries).
+__global__ void k_dump_terms(int model, TermSp up, TermSp dn, int64_t ddn, const hphi_term *terms, int nt,
+                             int64_t r0, int64_t nr, int stride, int64_t *cols, int8_t *signs, int32_t *tids,
+                             int32_t *cnt, int *bad) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nr; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = r0 + k;
+        uint64_t su, sd = 0;
+        if (model == HPHI_SPIN_HALF_GC) {
+            su = (uint64_t)r;
+        } else if (model == HPHI_SPIN_HALF) {
+            su = tsp_state(up, (uint64_t)r);
+        } else {
+            su = tsp_state(up, (uint64_t)(r / ddn));
+            sd = tsp_state(dn, (uint64_t)(r % ddn));
+        }
+        int n = 0;
+        int64_t *c = cols + k * stride;
+        int8_t *g = signs + k * stride;
+        int32_t *t = tids + k * stride;
+        for (int q = 0; q < nt; q++) {
+            const hphi_term T = terms[q];
+            const uint64_t m = (1ull << T.i) | (1ull << T.j);
+            if (T.kind == HPHI_EXCHANGE || T.kind == HPHI_XXZ) {
+                const double jxy = T.kind == HPHI_EXCHANGE ? T.v0 : T.v1;
+                if (jxy == 0.0 || __popcll(su & m) != 1) continue;
+                const uint64_t s2 = su ^ m;
+                const int64_t col = model == HPHI_SPIN_HALF_GC ? (int64_t)s2 : tsp_rank(up, s2);
+                if (col < 0) atomicExch(bad, 1);
+                c[n] = col;
+                g[n] = 1;
+                t[n] = q;
+                n++;
+            } else if (T.kind == HPHI_HOP) {
+                if (T.v0 == 0.0) continue;
+                const int lo = T.i < T.j ? T.i : T.j, hi = T.i < T.j ? T.j : T.i;
+                // occupied sites strictly between the ends
+                const uint64_t between = ((1ull << hi) - 1) & ~((2ull << lo) - 1);
+                for (int sp = 0; sp < 2; sp++) {
+                    if (T.spin != -1 && T.spin != sp) continue;
+                    const uint64_t s = sp ? sd : su;
+                    if (__popcll(s & m) != 1) continue;
+                    const uint64_t s2 = s ^ m;
+                    const int64_t a = sp ? tsp_rank(up, su) : tsp_rank(up, s2);
+                    const int64_t b = sp ? tsp_rank(dn, s2) : tsp_rank(dn, sd);
+                    if (a < 0 || b < 0) atomicExch(bad, 1);
+                    c[n] = a * ddn + b;
+                    g[n] = (__popcll(s & between) & 1) ? -1 : 1;
+                    t[n] = q;
+                    n++;
+                }
+            }
+        }
+        cnt[k] = n;
+    }
+}
+
 }  // namespace
 
 int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,
@@ -138,8 +229,8 @@ int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, st
 
 using namespace hphi;
 
-extern "C" int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1,
-                                 int64_t *rowptr, int64_t *cols_out, double *vals_out, int64_t *cap) {
+extern "C" int hphi_dump_pattern_merged(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1,
+                                        int64_t *rowptr, int64_t *cols_out, double *vals_out, int64_t *cap) {
     if (!ctx || !ham || !rowptr || !cap) return HPHI_E_INVAL;
     ctx->err.clear();
     if (row0 < 0 || row1 > ham->D || row0 >= row1) return set_err(ctx, HPHI_E_INVAL, "bad row range");
@@ -197,5 +288,108 @@ extern "C" int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row
     }
     rowptr[nr] = pos;
     *cap = pos;
+    return HPHI_OK;
+}
+
+extern "C" int hphi_dump_pattern(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, int64_t *rows_out,
+                                 int64_t *cols_out, int8_t *signs_out, int32_t *term_ids_out, int64_t *count) {
+    if (!ctx || !ham || !count) return HPHI_E_INVAL;
+    ctx->err.clear();
+    if (row0 < 0 || row1 > ham->D || row0 >= row1) return set_err(ctx, HPHI_E_INVAL, "bad row range");
+    if (row1 - row0 > (1 << 22)) return set_err(ctx, HPHI_E_INVAL, "at most 2^22 rows per dump");
+    HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
+    const hphi_basis *b = ham->basis;
+    const int nt = (int)ham->terms.size();
+    const int stride = nt > 0 ? 2 * nt : 1;
+    auto sp_of = [&](const Species &s) {
+        return TermSp{s.ja, s.jb, s.jbp, s.loff, s.lstate, s.N, s.n, s.nlo, s.nhi};
+    };
+    const TermSp up = b->model == HPHI_SPIN_HALF_GC ? TermSp{} : sp_of(b->sp[0]);
+    const TermSp dn = b->model == HPHI_HUBBARD ? sp_of(b->sp[1]) : TermSp{};
+    const int64_t ddn = b->model == HPHI_HUBBARD ? b->sp[1].dim : 1;
+    // rows in chunks of at most 2^24 entry slots
+    const int64_t total = row1 - row0;
+    int64_t chunk = ((int64_t)1 << 24) / stride;
+    if (chunk < 1) chunk = 1;
+    if (chunk > total) chunk = total;
+    hphi_term *dterm = nullptr;
+    int64_t *dc = nullptr;
+    int8_t *dg = nullptr;
+    int32_t *dt = nullptr, *dn_ = nullptr;
+    int *dbad = nullptr;
+    const size_t slots = (size_t)chunk * stride;
+    if (cudaMalloc(&dterm, sizeof(hphi_term) * (nt > 0 ? nt : 1)) != cudaSuccess ||
+        cudaMalloc(&dc, slots * 8) != cudaSuccess || cudaMalloc(&dg, slots) != cudaSuccess ||
+        cudaMalloc(&dt, slots * 4) != cudaSuccess || cudaMalloc(&dn_, (size_t)chunk * 4) != cudaSuccess ||
+        cudaMalloc(&dbad, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dterm);
+        cudaFree(dc);
+        cudaFree(dg);
+        cudaFree(dt);
+        cudaFree(dn_);
+        return set_err(ctx, HPHI_E_NOMEM, "pattern buffers");
+    }
+    std::vector<int64_t> hc(slots);
+    std::vector<int8_t> hg(slots);
+    std::vector<int32_t> ht(slots), hn(chunk);
+    const int64_t cap = *count;
+    const bool write = rows_out && cols_out && signs_out && term_ids_out;
+    int64_t pos = 0;
+    int bad = 0;
+    cudaError_t e = cudaSuccess;
+    if (nt > 0) e = cudaMemcpy(dterm, ham->terms.data(), sizeof(hphi_term) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(int), ctx->stream);
+    for (int64_t r0 = row0; r0 < row1 && e == cudaSuccess; r0 += chunk) {
+        const int64_t nr = (row1 - r0) < chunk ? (row1 - r0) : chunk;
+        const int grid = (int)((nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096);
+        k_dump_terms<<<grid, 256, 0, ctx->stream>>>(b->model, up, dn, ddn, dterm, nt, r0, nr, stride, dc, dg, dt,
+                                                     dn_, dbad);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(hn.data(), dn_, (size_t)nr * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && write) {
+            const size_t ns = (size_t)nr * stride;
+            e = cudaMemcpy(hc.data(), dc, ns * 8, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(hg.data(), dg, ns, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(ht.data(), dt, ns * 4, cudaMemcpyDeviceToHost);
+        }
+        if (e != cudaSuccess) break;
+        for (int64_t k = 0; k < nr; k++) {
+            const int n = hn[k];
+            if (n < 0 || n > stride) {
+                bad = 2;
+                break;
+            }
+            if (write && pos + n <= cap) {
+                for (int u = 0; u < n; u++) {
+                    rows_out[pos + u] = r0 + k;
+                    cols_out[pos + u] = hc[k * stride + u];
+                    signs_out[pos + u] = hg[k * stride + u];
+                    term_ids_out[pos + u] = ht[k * stride + u];
+                }
+            }
+            pos += n;
+        }
+        if (bad) break;
+    }
+    if (e == cudaSuccess && !bad) {
+        int fl = 0;
+        e = cudaMemcpy(&fl, dbad, sizeof(int), cudaMemcpyDeviceToHost);
+        if (fl) bad = 1;
+    }
+    cudaFree(dterm);
+    cudaFree(dc);
+    cudaFree(dg);
+    cudaFree(dt);
+    cudaFree(dn_);
+    cudaFree(dbad);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "pattern export");
+    if (bad) return set_err(ctx, HPHI_E_DEVICE_CHECK, "pattern export: a target state outside the sector");
+    if (!write || pos > cap) {
+        *count = pos;
+        return set_err(ctx, HPHI_E_INVAL, "pattern needs %lld entries", (long long)pos);
+    }
+    *count = pos;
     return HPHI_OK;
 }

@@ -669,7 +669,11 @@ int launch_copy(hphi_ctx *ctx, int real_dtype, int64_t n, int nr, const void *x,
 
 // ---- dot product with file-scope scratch (no device allocation) ------------
 // The partials of the block reduction and the reduced values live in a
-// file-scope device array; its device address is looked up once per device.
+// file-scope device array.  Host code cannot use the array's name as a device
+// address, so every call looks the address up (cudaGetSymbolAddress, a
+// host-side lookup that allocates nothing) with the target device current.
+// Nothing is cached, so the address stays valid across cudaDeviceReset and
+// concurrent first calls from several threads need no synchronisation.
 namespace {
 
 constexpr int kStaticReal = HPHI_DOT_STATIC_MAX_REAL;
@@ -679,14 +683,23 @@ static_assert(kStaticDoubles == 2 * kStaticBlocks * kStaticReal + 2 * kStaticRea
 
 static __device__ __align__(256) double g_dot_scratch[kStaticDoubles];
 
-double *g_dot_scratch_addr[64] = {nullptr};
+// 1 if p is device (or managed) memory that `device` can address directly.
+bool on_device(const void *p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
 
 }  // namespace
 
 extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, int nvec, const void *x, int64_t ldx,
                                const void *y, int64_t ldy, double *out) {
     using namespace hphi;
-    if (!out || n < 0 || nvec < 1 || !valid_dtype(dtype) || device < 0 || device >= 64) return HPHI_E_INVAL;
+    if (!out || n < 0 || nvec < 1 || !valid_dtype(dtype) || device < 0) return HPHI_E_INVAL;
     const int cpl = is_complex(dtype) ? 2 : 1, nr = nvec * cpl;
     if (nr > kStaticReal) return HPHI_E_INVAL;
     if (ldx < nvec || ldy < nvec || (n > 0 && (!x || !y))) return HPHI_E_INVAL;
@@ -694,6 +707,15 @@ extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, i
         for (int k = 0; k < nr; k++) out[k] = 0.0;
         return HPHI_OK;
     }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return HPHI_E_CUDA;
+    }
+    if (device >= ndev) return HPHI_E_INVAL;
+    // operands on another device (or in plain host memory) would be read
+    // through their unified addresses: refuse them instead
+    if (!on_device(x, device) || !on_device(y, device)) return HPHI_E_INVAL;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) {
         cudaGetLastError();
@@ -706,21 +728,20 @@ extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, i
             rc = HPHI_E_CUDA;
             break;
         }
-        if (!g_dot_scratch_addr[device]) {
-            double *p = nullptr;
-            if (cudaGetSymbolAddress((void **)&p, g_dot_scratch) != cudaSuccess || !p) {
-                rc = HPHI_E_CUDA;
-                break;
-            }
-            g_dot_scratch_addr[device] = p;
+        double *partials = nullptr;
+        if (cudaGetSymbolAddress((void **)&partials, g_dot_scratch) != cudaSuccess || !partials) {
+            rc = HPHI_E_CUDA;
+            break;
         }
-        double *partials = g_dot_scratch_addr[device];
         double *result = partials + 2 * kStaticBlocks * kStaticReal;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
             rc = HPHI_E_CUDA;
             break;
         }
+        // the grid of hphi_dot (vec_grid: SMs x 8 blocks at most), so that both
+        // entry points sum in the same order; devices with more than
+        // kStaticBlocks / 8 SMs get the capped grid (equal to rounding then)
         const int tpr = tpr_of(nr);
         int64_t g = (n + (kVT / tpr) - 1) / (kVT / tpr);
         int64_t cap = (int64_t)sms * 8;
@@ -734,12 +755,10 @@ extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, i
     k_dot<T, C><<<grid, kVT, 0, st>>>(n, nr, tpr, cpl == 2, (const T *)x, lx, (const T *)y, ly, partials)
         if (rd == HPHI_F64) {
             if (cplane <= 1) HPHI_SDOT(double, 1);
-            else if (cplane <= 2) HPHI_SDOT(double, 2);
-            else HPHI_SDOT(double, 4);
+            else HPHI_SDOT(double, 2);
         } else {
             if (cplane <= 1) HPHI_SDOT(float, 1);
-            else if (cplane <= 2) HPHI_SDOT(float, 2);
-            else HPHI_SDOT(float, 4);
+            else HPHI_SDOT(float, 2);
         }
 #undef HPHI_SDOT
         k_reduce<<<1, 256, 0, st>>>(partials, grid, 2 * nr, result);
@@ -767,4 +786,3 @@ extern "C" int hphi_dot_static(int device, void *stream, int dtype, int64_t n, i
     cudaSetDevice(prev);
     return rc;
 }
-

@@ -41,7 +41,7 @@ class _LanczosOpts(C.Structure):
 
 class _LanczosResult(C.Structure):
     _fields_ = [("e0", C.c_double), ("resid_est", C.c_double), ("resid", C.c_double), ("steps", C.c_int),
-                ("breakdown", C.c_int)]
+                ("breakdown", C.c_int), ("e0_rq", C.c_double)]
 
 
 class _KrylovOpts(C.Structure):
@@ -101,7 +101,8 @@ _SIGS = {
     "hphi_ham_autotune": (i32, [vp, vp, i32, i32, i32, C.POINTER(dbl), C.POINTER(i32)]),
     "hphi_apply_H": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, dbl, dbl]),
     "hphi_apply_H_host": (i32, [vp, vp, i32, i32, i64, vp, vp, dbl]),
-    "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
+    "hphi_dump_pattern": (i32, [vp, vp, i64, i64, vp, vp, vp, vp, C.POINTER(i64)]),
+    "hphi_dump_pattern_merged": (i32, [vp, vp, i64, i64, vp, vp, vp, C.POINTER(i64)]),
     "hphi_dot": (i32, [vp, i32, i64, i32, vp, i64, vp, i64, vp]),
     "hphi_nrm2": (i32, [vp, i32, i64, i32, vp, i64, vp]),
     "hphi_axpy": (i32, [vp, i32, i64, i32, vp, vp, i64, vp, i64]),
@@ -109,7 +110,8 @@ _SIGS = {
     "hphi_random_vector": (i32, [vp, i32, i64, i32, C.c_uint64, vp, i64]),
     "hphi_lanczos": (i32, [vp, vp, C.POINTER(_LanczosOpts), vp, vp, vp, vp, C.POINTER(_LanczosResult)]),
     "hphi_tpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
-    "hphi_mtpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, vp, vp, vp, vp]),
+    "hphi_mtpq_step": (i32, [vp, vp, i32, i32, vp, i64, dbl, i32, i32, vp, vp, vp, vp, vp]),
+    "hphi_tpq_bootstrap": (i32, [i32, i32, vp, vp, vp, vp, i32, i32, vp, C.c_uint64, vp, vp, vp, vp]),
     "hphi_lobpcg": (i32, [vp, vp, i32, vp, i32, dbl, vp, vp, C.POINTER(i32)]),
     "hphi_tridiag_eigen": (i32, [i32, vp, vp, vp, vp]),
     "hphi_dot_static": (i32, [i32, vp, i32, i64, i32, vp, i64, vp, i64, vp]),
@@ -125,6 +127,8 @@ _SIGS = {
     "hphi_server_get_stats": (i32, [vp, C.POINTER(_ServerStats)]),
     "hphi_shifted_krylov": (i32, [vp, vp, C.POINTER(_KrylovOpts), i32, vp, i64, i32, vp, vp, vp, vp, vp,
                                   C.POINTER(_KrylovResult)]),
+    "hphi_szz_spectrum": (i32, [vp, vp, C.POINTER(_KrylovOpts), vp, i32, vp, i32, vp, vp, vp, vp,
+                                C.POINTER(_KrylovResult)]),
 }
 
 
@@ -368,6 +372,10 @@ def hphi_dot_static(device: int, x, y) -> np.ndarray:
     memory (no context needed); runs on torch's current stream of `device`."""
     import torch
     lib = load_library()
+    if x.device != y.device or not x.is_cuda or x.device.index != device:
+        raise ValueError(f"x and y must both be on cuda:{device}")
+    if x.dtype != y.dtype or x.shape != y.shape:
+        raise ValueError("x and y must have the same dtype and shape")
     px, nv, ldx = _vec(x)
     py, _, ldy = _vec(y)
     dc = _dtype_code(x)
@@ -439,7 +447,7 @@ def hphi_lanczos(ham: Hamiltonian, v0, max_steps: int, tol: float, check_every: 
         ctx.check(st)
     m = res.steps
     return dict(converged=st == HPHI_OK, status=st, e0=res.e0, resid_est=res.resid_est, resid=res.resid, steps=m,
-                breakdown=bool(res.breakdown), alpha=alpha[:m], beta=beta[1:m + 1])
+                breakdown=bool(res.breakdown), alpha=alpha[:m], beta=beta[1:m + 1], e0_rq=res.e0_rq)
 
 
 def hphi_lanczos_batch(hams, v0s, max_steps: int, tol: float, check_every: int = 8, gs_outs=None):
@@ -637,29 +645,35 @@ def hphi_shifted_krylov(ham: Hamiltonian, B, z, max_steps: int, tol: float, chec
                 max_resid=res.max_resid, alpha=alpha.reshape(nc, max_steps), beta=beta.reshape(nc, max_steps + 1))
 
 
-def hphi_szz_spectrum(ham: Hamiltonian, basis: Basis, gs, qs, z, max_steps: int, tol: float,
-                      check_every: int = 4):
+def hphi_szz_spectrum(ham: Hamiltonian, gs, qs, z, max_steps: int, tol: float, check_every: int = 4):
     """S^zz(q, z) = -Im <Phi_q|(z - H)^{-1}|Phi_q>, Phi_q = sum_l e^{i q l} S^z_l gs,
-    for every wave number in qs at once: the excitations fill the real block
-    [D][2 nq] (Re, Im of each q) and one shifted-Krylov run covers all columns.
-    Returns (S [nq][nz], D [nq][nz] complex, the shifted-Krylov dict)."""
-    import torch
-    qs = np.atleast_1d(np.asarray(qs, dtype=np.float64))
-    nq = qs.size
-    L = basis.n_sites
-    ph = [np.exp(1j * q * np.arange(L)) for q in qs]
-    # the imaginary part of e^{i q l} vanishes for q = 0 and q = pi (up to
-    # rounding of sin): those wave numbers need one real column
-    two = [bool(np.abs(p.imag).max() > 1e-12) for p in ph]
-    col = np.concatenate([[0], np.cumsum([2 if t else 1 for t in two])])
-    blk = torch.empty((basis.dim, 2 * nq), dtype=gs.dtype, device=gs.device)
-    for k in range(nq):
-        hphi_apply_sz_sum(basis, gs, blk[:, 2 * k:2 * k + 2], ph[k] if two[k] else ph[k].real)
-    keep = [2 * k + j for k in range(nq) for j in range(2 if two[k] else 1)]
-    rhs = blk[:, keep].contiguous()
-    r = hphi_shifted_krylov(ham, rhs, z, max_steps, tol, check_every)
-    Dq = np.stack([r["G"][col[k]] + (r["G"][col[k] + 1] if two[k] else 0.0) for k in range(nq)])
-    return -Dq.imag, Dq, r
+    for every wave number in qs at once (one shifted-Krylov run of all
+    excitation columns inside the library).  gs: real contiguous CUDA vector
+    (F64/F32).  Returns (S [nq][nz], D [nq][nz] complex, dict with resid
+    [nq][nz], steps, converged, status, max_resid); NOTCONV is reported."""
+    ctx = ham.ctx
+    if not gs.is_cuda or gs.dim() != 1 or gs.stride(0) != 1 or gs.numel() != ham.dim:
+        raise ValueError("gs must be a contiguous CUDA vector of the Hamiltonian's dimension")
+    dc = _dtype_code(gs)
+    if dc not in (F64, F32):
+        raise ValueError("gs must be real (F64 or F32)")
+    q = np.ascontiguousarray(np.atleast_1d(np.asarray(qs, dtype=np.float64)))
+    zz = np.asarray(z, dtype=np.complex128).reshape(-1)
+    zh = np.ascontiguousarray(np.stack([zz.real, zz.imag], axis=1).reshape(-1))
+    nq, nz = q.size, zz.size
+    S = np.zeros(nq * nz)
+    Dh = np.zeros(2 * nq * nz)
+    rs = np.zeros(nq * nz)
+    opts = _KrylovOpts(max_steps, tol, dc, check_every)
+    res = _KrylovResult()
+    ctx._sync_stream()
+    st = ctx.lib.hphi_szz_spectrum(ctx.h, ham.h, C.byref(opts), C.c_void_p(gs.data_ptr()), nq, _np(q), nz, _np(zh),
+                                   _np(S), _np(Dh), _np(rs), C.byref(res))
+    if st not in (HPHI_OK, -4):
+        ctx.check(st)
+    Dq = (Dh[0::2] + 1j * Dh[1::2]).reshape(nq, nz)
+    return S.reshape(nq, nz), Dq, dict(resid=rs.reshape(nq, nz), steps=res.steps, converged=bool(res.converged),
+                                       status=st, max_resid=res.max_resid)
 
 
 def hphi_lobpcg(ham: Hamiltonian, X, max_iter: int, tol: float):
@@ -679,64 +693,79 @@ def hphi_lobpcg(ham: Hamiltonian, X, max_iter: int, tol: float):
     return dict(evals=ev, resid=rs, iters=it.value, converged=st == HPHI_OK, status=st)
 
 
-def hphi_mtpq_step(ham: Hamiltonian, V, l: float, n_sites: int, norm2: np.ndarray):
-    """One microcanonical TPQ step in place on V (U_m = 1 - H / (l N_s)); norm2
-    is updated in place.  Returns (e, h2, logd) of the state before the step."""
+def hphi_mtpq_step(ham: Hamiltonian, V, l: float, n_sites: int, k: int, norm2: np.ndarray):
+    """One microcanonical TPQ step in place on V (U_m = 1 - H / (l N_s)) from
+    the state of step index k; norm2 is updated in place.  Returns (e, h2,
+    logd, beta) of the state before the step, beta_k from the library."""
     ctx = ham.ctx
     pv, nv, ld = _vec(V)
     assert norm2.dtype == np.float64 and norm2.size == nv and norm2.flags.c_contiguous
-    e, h2, logd = np.zeros(nv), np.zeros(nv), np.zeros(nv)
+    e, h2, logd, beta = np.zeros(nv), np.zeros(nv), np.zeros(nv), np.zeros(nv)
     ctx._sync_stream()
-    ctx.check(ctx.lib.hphi_mtpq_step(ctx.h, ham.h, _dtype_code(V), nv, pv, ld, float(l), int(n_sites), _np(norm2),
-                                     _np(e), _np(h2), _np(logd)))
-    return e, h2, logd
+    ctx.check(ctx.lib.hphi_mtpq_step(ctx.h, ham.h, _dtype_code(V), nv, pv, ld, float(l), int(n_sites), int(k),
+                                     _np(norm2), _np(e), _np(h2), _np(logd), _np(beta)))
+    return e, h2, logd, beta
 
 
-def tpq_thermo(e, h2, log_norm, P: int, M: int, seed: int = 1):
-    """E(beta_k) and C(beta_k) / beta_k^2 of cTPQ samples by the bootstrap of
-    Sec. 3.5.1: M resamplings of P sample indices (drawn with replacement);
-    each resampling weights sample n at step k by its norm N_k^n relative to
-    sample 0's, <A>_m = sum_n w_n A_n / sum_n w_n; returns (mean, sd) of <H>
-    and of <H^2> - <H>^2 over the M resamplings, sd with 1/(M - 1).
-    Inputs [n_samples][n_steps]: <H>, <H^2> per sample and log N_k."""
-    e, h2, ln = (np.asarray(a, dtype=np.float64) for a in (e, h2, log_norm))
-    rng = np.random.default_rng(seed)
-    draws = rng.integers(0, e.shape[0], size=(M, P))
-    rel = np.exp(ln - ln[0:1, :])
-    hm = np.empty((M, e.shape[1]))
-    fm = np.empty((M, e.shape[1]))
-    for i in range(M):
-        w = rel[draws[i]]
-        z = w.sum(axis=0)
-        a1 = (w * e[draws[i]]).sum(axis=0) / z
-        a2 = (w * h2[draws[i]]).sum(axis=0) / z
-        hm[i], fm[i] = a1, a2 - a1 * a1
-
-    def msd(a):
-        mu = a.mean(axis=0)
-        return mu, (np.sqrt(((a - mu) ** 2).sum(axis=0) / (M - 1)) if M > 1 else np.zeros_like(mu))
-    return msd(hm), msd(fm)
-
-
-def mtpq_beta(k: int, l: float, n_sites: int, e) -> np.ndarray:
-    """beta_k = k dtau / (1 - u_k / l), dtau = 2 / (l N_s), u_k = e / N_s (Sec. 3.5.1)."""
-    dtau = 2.0 / (l * n_sites)
-    return k * dtau / (1.0 - np.asarray(e) / n_sites / l)
+def hphi_tpq_bootstrap(e, h2, log_norm, P: int, M: int, beta=None, picks=None, seed: int = 1):
+    """E(beta_k), C(beta_k) with standard deviations from TPQ samples by the
+    paper's bootstrap (computed in the library).  e, h2, log_norm:
+    [n_samples][n_temps]; beta: [n_temps] or None (then C is returned without
+    beta^2); picks: [M][P] sample indices or None (Philox draws of seed).
+    Returns dict(e_mean, e_sd, c_mean, c_sd)."""
+    lib = load_library()
+    e, h2, ln = (np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (e, h2, log_norm))
+    if e.ndim != 2 or h2.shape != e.shape or ln.shape != e.shape:
+        raise ValueError("e, h2 and log_norm must share one [n_samples][n_temps] shape")
+    ns, nk = e.shape
+    b = None if beta is None else np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
+    if b is not None and b.size != nk:
+        raise ValueError("one beta per temperature")
+    pk = None if picks is None else np.ascontiguousarray(np.asarray(picks, dtype=np.int32).reshape(M, P))
+    out = {k: np.zeros(nk) for k in ("e_mean", "e_sd", "c_mean", "c_sd")}
+    st = lib.hphi_tpq_bootstrap(ns, nk, _np(e), _np(h2), _np(ln), _np(b) if b is not None else None, int(P), int(M),
+                                _np(pk) if pk is not None else None, C.c_uint64(seed), _np(out["e_mean"]),
+                                _np(out["e_sd"]), _np(out["c_mean"]), _np(out["c_sd"]))
+    if st != HPHI_OK:
+        raise HphiError(st, "hphi_tpq_bootstrap failed")
+    return out
 
 
 def hphi_dump_pattern(ham: Hamiltonian, row0: int, row1: int):
+    """Unmerged off-diagonal pattern of rows [row0, row1) in (row, term) order:
+    host arrays rows, cols, signs (int8), term_ids (int32)."""
+    ctx = ham.ctx
+    cnt = i64(0)
+    ctx._sync_stream()
+    st = ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, None, None, None, None, C.byref(cnt))
+    if st not in (HPHI_OK, -1) or cnt.value < 0:
+        ctx.check(st)
+    n = cnt.value
+    rows = np.zeros(max(n, 1), np.int64)
+    cols = np.zeros(max(n, 1), np.int64)
+    signs = np.zeros(max(n, 1), np.int8)
+    tids = np.zeros(max(n, 1), np.int32)
+    cnt = i64(max(n, 1))
+    ctx.check(ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, _np(rows), _np(cols), _np(signs), _np(tids),
+                                        C.byref(cnt)))
+    n = cnt.value
+    return rows[:n], cols[:n], signs[:n], tids[:n]
+
+
+def hphi_dump_pattern_merged(ham: Hamiltonian, row0: int, row1: int):
     """Merged, column-sorted pattern of rows [row0, row1) as host CSR arrays."""
     ctx = ham.ctx
     n = row1 - row0
     rowptr = np.zeros(n + 1, np.int64)
     cap = i64(0)
     ctx._sync_stream()
-    st = ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, _np(rowptr), None, None, C.byref(cap))
+    st = ctx.lib.hphi_dump_pattern_merged(ctx.h, ham.h, row0, row1, _np(rowptr), None, None, C.byref(cap))
     if st not in (HPHI_OK, -1) or cap.value <= 0:
         ctx.check(st)
     cols = np.zeros(cap.value, np.int64)
     vals = np.zeros(cap.value, np.float64)
-    ctx.check(ctx.lib.hphi_dump_pattern(ctx.h, ham.h, row0, row1, _np(rowptr), _np(cols), _np(vals), C.byref(cap)))
+    ctx.check(ctx.lib.hphi_dump_pattern_merged(ctx.h, ham.h, row0, row1, _np(rowptr), _np(cols), _np(vals),
+                                               C.byref(cap)))
     return rowptr, cols[:cap.value], vals[:cap.value]
 
 

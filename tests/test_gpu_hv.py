@@ -312,3 +312,67 @@ def test_last_kernel_names_the_launch():
     h.set_tuning(variant=0)
     hphi.hphi_apply_H(h, x, y)
     assert h.ctx.last_kernel().startswith("k_hvl<f32,")
+
+
+@pytest.mark.parametrize("N,nup", [(2, 1), (5, 2), (9, 4), (12, 6), (13, 4), (17, 8), (20, 7), (22, 11), (24, 12)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_segment_kernel(N, nup, dtype):
+    """Two-pass segment kernel (spin sector, one column): low halves of 1 to
+    12 bits (l1 of 0 to 4 bits), every popcount class, random XXZ couplings
+    incl. zero Jxy, so every bond class (high-high, low-high on either part,
+    within and across the parts of the low half) with and without terms; the
+    accumulate form (beta != 0) takes the context buffer, the plain one y."""
+    rng = random.Random(N * 41 + nup)
+    pairs = list(itertools.combinations(range(N), 2))
+    pairs = rng.sample(pairs, min(len(pairs), 3 * N))
+    terms = [("XXZ", i, j, 0, rng.uniform(-1, 2), rng.uniform(-1, 2) if k % 7 else 0.0)
+             for k, (i, j) in enumerate(pairs)]
+    m, b, h = pair("SPIN_HALF", N, nup, 0, terms)
+    h.set_tuning(variant=4)
+    _check(m, h, dtype, 1, alpha=0.8, beta=0.0, seed=N)
+    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<"), h.ctx.last_kernel()
+    _check(m, h, dtype, 1, alpha=-1.1, beta=0.35, seed=N + 1)
+
+
+@pytest.mark.parametrize("Lx,Ly", [(4, 4), (6, 4), (5, 5), (6, 5)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_segment_kernel_square_lattices(Lx, Ly, dtype):
+    """Periodic square lattices up to 30 sites (S^z = 0): the lattice bonds
+    fall into every class at the split the kernel takes."""
+    N = Lx * Ly
+    m, b, h = pair("SPIN_HALF", N, N // 2, 0, heisenberg_terms(square(Lx, Ly), 1.0))
+    h.set_tuning(variant=4)
+    if m.dim <= 3_000_000:
+        _check(m, h, dtype, 1, alpha=1.0, beta=0.0, seed=N)
+    else:
+        rng = np.random.default_rng(N)
+        rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 300)])
+        assert _sampled_rows(m, h, dtype, 1, rows, 60 + N) < (1e-15 if dtype == torch.float64 else 1e-6)
+    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_segment_square_4x8_full_size_sampled(dtype):
+    m, b, h = pair("SPIN_HALF", 32, 16, 0, heisenberg_terms(square(8, 4), 1.0))
+    h.set_tuning(variant=4)
+    rng = np.random.default_rng(29)
+    rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
+    assert _sampled_rows(m, h, dtype, 1, rows, 63) < (1e-15 if dtype == torch.float64 else 1e-6)
+    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<")
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_fused_reductions_one_column_sector(variant):
+    """<x, Hx>, |Hx|^2, |x|^2 of one sector column (the cTPQ step on one
+    column and the FP64 Rayleigh quotient take this launch form)."""
+    m, b, h = pair("SPIN_HALF", 16, 8, 0, heisenberg_terms(square(4, 4), 1.0))
+    h.set_tuning(variant=variant)
+    V0 = random_vectors(m.dim, 1, 5)
+    Vg = torch.from_numpy(V0).cuda().contiguous()
+    Vo = V0.copy()
+    norm2 = np.zeros(1)
+    for _ in range(4):
+        e, h2, logd = hphi.hphi_tpq_step(h, Vg, 0.05, 6, norm2)
+        eo, h2o, do = m.tpq_step(Vo, 0.05, 6)
+        assert np.allclose(e, eo, rtol=1e-12) and np.allclose(h2, h2o, rtol=1e-12)
+        assert np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)

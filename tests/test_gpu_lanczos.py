@@ -23,6 +23,7 @@ def test_chain16_sz0_fp64():
     assert abs(r["e0"] - ro["e0"]) <= 1e-10 * abs(ro["e0"])
     assert abs(np.dot(gs.cpu().numpy(), ro["gs"])) >= 1 - 1e-10
     assert r["resid"] < 1e-9
+    assert abs(r["e0_rq"] - ro["e0"]) <= 1e-12 * abs(ro["e0"])
     # alpha/beta agree with the oracle's recurrence along the run
     k = min(r["steps"], ro["steps"], 40)
     assert np.allclose(r["alpha"][:k], ro["alpha"][:k], rtol=1e-9, atol=1e-9)
@@ -37,6 +38,13 @@ def test_chain16_fp32_storage_error_stated():
     r = hphi.hphi_lanczos(h, torch.from_numpy(v0).float().cuda(), 300, 1e-6, gs_out=gs)
     err = abs(r["e0"] - ro["e0"]) / abs(ro["e0"])
     assert err < 1e-6, err
+    # the FP64 Rayleigh quotient of the FP32 ground-state vector: error quadratic
+    # in the vector's error
+    err_rq = abs(r["e0_rq"] - ro["e0"]) / abs(ro["e0"])
+    assert err_rq < 1e-10, (err_rq, err)
+    # and it is computed from the vector the call returns
+    x = gs.double().cpu().numpy()
+    assert abs(r["e0_rq"] - x @ m.apply(x) / (x @ x)) < 1e-12 * abs(ro["e0"])
 
 
 @pytest.mark.parametrize("N,seed", [(10, 1), (12, 2)])
@@ -105,6 +113,8 @@ def test_reorth_hubbard_and_chain_vs_oracle(dtype, tol):
         assert r["converged"], r
         assert abs(r["e0"] - ro["e0"]) <= tol * abs(ro["e0"]), (model, r["e0"], ro["e0"])
         assert r["resid"] < (1e-8 if dtype == torch.float64 else 1e-3) * max(1.0, abs(r["e0"]))
+        # FP64 Rayleigh quotient of the returned vector: 1e-10 even for FP32 storage
+        assert abs(r["e0_rq"] - ro["e0"]) <= 1e-10 * abs(ro["e0"]), (model, dtype, r["e0_rq"], ro["e0"])
 
 
 def test_reorth_storage_beyond_device_memory_is_nomem():
@@ -119,7 +129,7 @@ def test_reorth_storage_beyond_device_memory_is_nomem():
     assert ei.value.code == -2
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4])
 def test_chain16_each_single_column_kernel(variant):
     """The fused Lanczos step (reductions <x,y> and |y|^2 of the ground-state
     pass) through the table-driven and the staged kernels."""
@@ -132,3 +142,36 @@ def test_chain16_each_single_column_kernel(variant):
     r = hphi.hphi_lanczos(h, torch.from_numpy(v0).cuda(), cfg["max_steps"], cfg["tol"], gs_out=gs)
     assert r["converged"] and abs(r["e0"] - ro["e0"]) <= 1e-10 * abs(ro["e0"])
     assert abs(np.dot(gs.cpu().numpy(), ro["gs"])) >= 1 - 1e-10 and r["resid"] < 1e-9
+
+
+def test_hubbard4x4_energy_against_the_oracle_golden():
+    """The 4x4 Hubbard workload (t = 1, U = 8, half filling, 165,636,900
+    states) at full size against the oracle's FP64 Lanczos run from the same
+    seeded start vector (tests/golden/lanczos_hubbard4x4_U8.json, written by
+    tests/golden/make_lanczos_golden.py, which calls only the oracle):
+      FP64 vectors with full reorthogonalisation: E0 to 1e-10 relative, the
+      first 20 alpha of the two recurrences to 1e-9;
+      FP32 vectors (FP64 alpha/beta, reorthogonalisation dots, tridiagonal
+      problem): the Ritz value's error stated, and the FP64 Rayleigh
+      quotient of the FP32 ground-state vector within 1e-8 (the mixed-
+      precision target)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lanczos_hubbard4x4_U8.json")))
+    cfg = configs.hubbard_square4x4()
+    m, b, h = pair(cfg["model"], cfg["n_sites"], cfg["n_up"], cfg["n_dn"], cfg["terms"])
+    assert b.dim == gold["dim"] and gold["seed"] == cfg["seed"]
+    v0 = torch.empty(b.dim, dtype=torch.float64, device="cuda")
+    hphi.hphi_random_vector(h.ctx, v0, cfg["seed"])
+    r64 = hphi.hphi_lanczos(h, v0, cfg["max_steps"], cfg["tol"], check_every=5, reorth=True)
+    e0 = gold["e0"]
+    assert r64["converged"] and abs(r64["e0"] - e0) <= 1e-10 * abs(e0), (r64["e0"], e0)
+    k = 20
+    assert np.allclose(r64["alpha"][:k], gold["alpha"][:k], rtol=1e-9, atol=1e-9)
+    gs = torch.empty(b.dim, dtype=torch.float32, device="cuda")
+    r32 = hphi.hphi_lanczos(h, v0.float(), cfg["max_steps"], cfg["tol"], check_every=5, gs_out=gs, reorth=True)
+    err_ritz = abs(r32["e0"] - e0) / abs(e0)
+    err_rq = abs(r32["e0_rq"] - e0) / abs(e0)
+    print(f"4x4 Hubbard FP32 storage: Ritz value error {err_ritz:.2e}, FP64 Rayleigh quotient error {err_rq:.2e}")
+    assert err_ritz < 1e-6
+    assert err_rq <= 1e-8, (err_rq, err_ritz)

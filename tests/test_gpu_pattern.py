@@ -14,10 +14,19 @@ pytestmark = pytest.mark.gpu
 
 def _cmp(m, h, r0, r1):
     orp, oc, ov = m.pattern(r0, r1)
-    grp, gc, gv = hphi.hphi_dump_pattern(h, r0, r1)
+    grp, gc, gv = hphi.hphi_dump_pattern_merged(h, r0, r1)
+    _cmp_terms(m, h, r0, r1)
     assert np.array_equal(grp - grp[0], orp - orp[0])
     assert np.array_equal(gc, oc)
     assert np.allclose(gv, ov, rtol=1e-14, atol=1e-14)
+
+
+def _cmp_terms(m, h, r0, r1):
+    """The unmerged (row, col, sign, term id) pattern, bit-exact."""
+    orow, ocol, osg, otid = m.pattern_terms(r0, r1)
+    grow, gcol, gsg, gtid = hphi.hphi_dump_pattern(h, r0, r1)
+    assert np.array_equal(grow, orow) and np.array_equal(gcol, ocol)
+    assert np.array_equal(gsg, osg) and np.array_equal(gtid, otid)
 
 
 def _random_spin_terms(N, nb, seed):
@@ -75,3 +84,36 @@ def test_rrg_gc_sampled_rows():
     m, b, h = pair("SPIN_HALF_GC", 26, 0, 0, terms)
     for r0 in (0, 12345678, (1 << 26) - 500):
         _cmp(m, h, r0, r0 + 500)
+
+
+@pytest.mark.parametrize("N,nu,nd,seed", [(6, 3, 3, 7), (8, 4, 3, 8), (10, 5, 5, 9)])
+def test_hubbard_terms_with_duplicates_and_cancellations(N, nu, nd, seed):
+    """Duplicate hops, a hop listed with the opposite orientation and a
+    cancelling pair (t and -t on the same bond): every term keeps its own
+    entries, signs included, bit for bit; the merged matrix still agrees."""
+    rng = random.Random(seed)
+    pairs = rng.sample(list(itertools.combinations(range(N), 2)), 6)
+    terms = [("HOP", i, j, -1, rng.uniform(0.5, 1.5), 0.0) for (i, j) in pairs]
+    i, j = pairs[0]
+    terms.append(("HOP", j, i, -1, terms[0][4], 0.0))          # duplicate, reversed
+    terms.append(("HOP", pairs[1][0], pairs[1][1], 0, 0.8, 0.0))
+    terms.append(("HOP", pairs[1][0], pairs[1][1], 0, -0.8, 0.0))  # cancels the previous one
+    terms.append(("HOP", 0, N - 1, 1, 1.1, 0.0))                # long hop: long fermion strings
+    terms += [("HUBBARD_U", s, s, 0, 4.0, 0.0) for s in range(N)]
+    m, b, h = pair("HUBBARD", N, nu, nd, terms)
+    rows, cols, signs, tids = hphi.hphi_dump_pattern(h, 0, m.dim)
+    assert -1 in signs and 1 in signs
+    _cmp(m, h, 0, m.dim)
+
+
+def test_pattern_export_capacity_and_range_errors():
+    m, b, h = pair("SPIN_HALF", 8, 4, 0, heisenberg_terms(chain(8), 1.0))
+    ctx = h.ctx
+    import ctypes as C
+    cnt = C.c_int64(0)
+    st = ctx.lib.hphi_dump_pattern(ctx.h, h.h, 0, 5, None, None, None, None, C.byref(cnt))
+    assert st == -1 and cnt.value == len(m.pattern_terms(0, 5)[0])
+    with pytest.raises(hphi.HphiError):
+        hphi.hphi_dump_pattern(h, 5, 5)
+    with pytest.raises(hphi.HphiError):
+        hphi.hphi_dump_pattern(h, 0, m.dim + 1)

@@ -81,10 +81,10 @@ def test_mtpq_steps_match_oracle(dtype):
     norm2 = np.zeros(4)
     tol = 1e-11 if dtype == torch.float64 else 2e-5
     for step in range(20):
-        e, h2, logd = hphi.hphi_mtpq_step(h, Vg, l, N, norm2)
+        e, h2, logd, beta = hphi.hphi_mtpq_step(h, Vg, l, N, step, norm2)
         eo, h2o, do = m.tpq_step(Vo, 2.0 / (l * N), 1)
         assert np.allclose(e, eo, rtol=tol, atol=tol) and np.allclose(logd, np.log(do), rtol=tol, atol=tol), step
-        beta = hphi.mtpq_beta(step, l, N, e)
+        # beta_k = k dtau / (1 - u_k / l) of the oracle's energy (Sec. 3.5.1)
         assert np.allclose(beta, step * (2.0 / (l * N)) / (1.0 - eo / N / l), rtol=tol, atol=tol)
 
 
@@ -113,11 +113,40 @@ def test_ctpq_thermodynamics_small_member_of_the_benchmark_family(dtype):
         E[:, k], E2[:, k], logn[:, k] = e, h2, acc
         acc = acc + logd
     betas = dtau * np.arange(steps)
-    bs = O.bootstrap_tpq(E, E2, logn, P=nvec, M=nvec // 2, seed=1)
-    mean, sd = bs["H"]
-    fl, fsd = bs["fluct"]
+    bs = hphi.hphi_tpq_bootstrap(E, E2, logn, P=nvec, M=nvec // 2, beta=betas, seed=1)
+    mean, sd, c, csd = bs["e_mean"], bs["e_sd"], bs["c_mean"], bs["c_sd"]
     for k in (50, 250, 500, 999):
         ex, cx = O.canonical_thermo(evals, np.array([1.0 / betas[k]]))
         assert abs(mean[k] - ex[0]) < 4 * sd[k] + 0.02 * abs(ex[0]), (k, mean[k], ex[0], sd[k])
-        c = betas[k] ** 2 * fl[k]
-        assert abs(c - cx[0]) < 4 * betas[k] ** 2 * fsd[k] + 0.1 * abs(cx[0]) + 0.02, (k, c, cx[0])
+        assert abs(c[k] - cx[0]) < 4 * csd[k] + 0.1 * abs(cx[0]) + 0.02, (k, c[k], cx[0])
+
+
+def test_ctpq_benchmark_trajectories_at_full_size():
+    """The cTPQ benchmark at its own size: 2^26 states of the seeded 26-site
+    random 3-regular graph (J ~ U[0.5, 1.5]), 16 complex FP64 start vectors
+    from the library's Philox stream, nmax = 6, dtau = 0.02 (Sec. 3.5.2).
+    Two of the 16 columns (0 and 9) are run by the oracle's literal Taylor sum
+    for the first 10 steps: <H> per step to 1e-10 of the energy scale
+    sqrt(<H^2>), <H^2> to 1e-10 relative, log D to 1e-11 absolute, and the
+    normalised vectors after the last step to 1e-10 of their largest entry."""
+    from workloads import configs
+    cfg = configs.ctpq_random_regular()
+    m, b, h = pair("SPIN_HALF_GC", cfg["n_sites"], 0, 0, cfg["terms"])
+    nvec, cols, steps = cfg["n_vec"], [0, 9], 10
+    V = torch.empty((m.dim, nvec), dtype=torch.complex128, device="cuda")
+    hphi.hphi_random_vector(h.ctx, V, cfg["seed"])
+    Vo = np.ascontiguousarray(V[:, cols].cpu().numpy())
+    Vo /= np.linalg.norm(Vo, axis=0, keepdims=True)
+    norm2 = np.zeros(nvec)
+    for step in range(steps):
+        e, h2, logd = hphi.hphi_tpq_step(h, V, cfg["dtau"], cfg["nmax"], norm2)
+        eo, h2o, do = m.tpq_step(Vo, cfg["dtau"], cfg["nmax"])
+        scale = np.sqrt(h2o)  # the energy scale of the state
+        assert np.all(np.abs(e[cols] - eo) <= 1e-10 * scale), (step, e[cols], eo)
+        assert np.allclose(h2[cols], h2o, rtol=1e-10, atol=0), (step, h2[cols], h2o)
+        # log D_k is O(dtau^2 <H^2>) near beta = 0: compared absolutely (FP64 norms
+        # summed over 2^27 reals carry ~1e-12 of rounding on either side)
+        assert np.all(np.abs(logd[cols] - np.log(do)) <= 1e-11), (step, logd[cols], np.log(do))
+    got = V[:, cols].cpu().numpy() / np.sqrt(norm2[cols])
+    assert np.abs(got - Vo).max() <= 1e-10 * np.abs(Vo).max()
+

@@ -77,3 +77,39 @@ def test_no_gpu_means_loud_failure():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         hphi.Context(0)
+
+
+def test_library_bootstrap_matches_the_oracle(lib):
+    """hphi_tpq_bootstrap (host code of the library) against the oracle's
+    bootstrap on random sample data, with the same explicit resamplings and
+    with the seeded draws (library Philox vs the input generator's)."""
+    import oracle as O
+    from workloads import bootstrap_picks
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=(12, 30))
+    h2 = e * e + rng.random(size=(12, 30))
+    ln = np.cumsum(rng.normal(scale=0.1, size=(12, 30)), axis=1)
+    beta = 0.05 * np.arange(30)
+    for picks in (rng.integers(0, 12, size=(6, 12)), None):
+        got = hphi.hphi_tpq_bootstrap(e, h2, ln, P=12, M=6, beta=beta, picks=picks, seed=5)
+        ref = O.bootstrap_tpq(e, h2, ln, P=12, M=6, picks=picks if picks is not None else bootstrap_picks(6, 12, 12, 5))
+        assert np.allclose(got["e_mean"], ref["H"][0], rtol=1e-13) and np.allclose(got["e_sd"], ref["H"][1], rtol=1e-11)
+        assert np.allclose(got["c_mean"], beta ** 2 * ref["fluct"][0], rtol=1e-12, atol=1e-15)
+        assert np.allclose(got["c_sd"], beta ** 2 * ref["fluct"][1], rtol=1e-10, atol=1e-15)
+
+
+def test_library_bootstrap_hand_case_and_errors(lib):
+    """The four ordered resamplings of two samples (weights 1, 3; <H> = 1, 2):
+    mean 13/8, sigma^2 = (9/16)/(M-1) = 3/16; bad picks are refused."""
+    import math
+    e = np.array([[1.0], [2.0]])
+    h2 = np.array([[2.0], [5.0]])
+    ln = np.array([[0.0], [math.log(3.0)]])
+    picks = np.array([[0, 0], [0, 1], [1, 0], [1, 1]])
+    got = hphi.hphi_tpq_bootstrap(e, h2, ln, P=2, M=4, picks=picks)
+    assert got["e_mean"][0] == pytest.approx(13 / 8, rel=1e-15)
+    assert got["e_sd"][0] == pytest.approx(math.sqrt(3 / 16), rel=1e-14)
+    assert got["c_mean"][0] == pytest.approx(35 / 32, rel=1e-15)
+    assert got["c_sd"][0] == pytest.approx(math.sqrt(3 / 256), rel=1e-13)
+    with pytest.raises(hphi.HphiError):
+        hphi.hphi_tpq_bootstrap(e, h2, ln, P=2, M=1, picks=np.array([[0, 2]]))

@@ -178,3 +178,48 @@ def test_invalid_models_rejected():
         O.Model("SPIN_HALF", 4, 2, 0, [("EXCHANGE", 0, 0, 0, 1.0, 0.0)])
     with pytest.raises(ValueError):
         O.Model("SPIN_HALF", 4, 2, 0, [("EXCHANGE", 0, 4, 0, 1.0, 0.0)])
+
+
+@pytest.mark.parametrize("N,nu,nd,seed", [(4, 2, 2, 11), (5, 2, 3, 12), (6, 3, 2, 13)])
+def test_pattern_terms_signs_and_ids_match_jordan_wigner(N, nu, nd, seed):
+    """Every off-diagonal entry of the unmerged pattern, sign x (-t of its
+    term), equals the Jordan-Wigner matrix element, and the bits its term
+    moves are the ones row and column differ in.  Hops are on distinct pairs
+    so that each (row, col) has a single source term."""
+    rng = random.Random(seed)
+    pairs = rng.sample(list(itertools.combinations(range(N), 2)), min(6, N * (N - 1) // 2))
+    terms = []
+    for (i, j) in pairs:
+        a, b = (i, j) if rng.random() < 0.5 else (j, i)
+        terms.append(("HOP", a, b, rng.choice([-1, 0, 1]), rng.uniform(0.5, 1.5), 0.0))
+    terms.append(("HUBBARD_U", 0, 0, 0, 3.0, 0.0))
+    m = O.Model("HUBBARD", N, nu, nd, terms)
+    Hk = project(hubbard_hamiltonian(N, terms), hubbard_sector_indices(N, nu, nd))
+    rows, cols, signs, tids = m.pattern_terms(0, m.dim)
+    assert len(rows) > 0 and set(np.unique(signs)) <= {-1, 1}
+    assert -1 in signs  # the cases reach odd fermion strings
+    order = np.lexsort((tids, rows))
+    assert np.array_equal(order, np.arange(len(rows)))  # (row, term) order
+    mask = (1 << N) - 1
+    for r, c, sg, k in zip(rows, cols, signs, tids):
+        kind, i, j, spin, t, _ = terms[k]
+        assert kind == "HOP"
+        assert Hk[r, c] == pytest.approx(-t * sg, abs=1e-14)
+        su, sd = m.row_state(int(r))
+        cu, cd = m.row_state(int(c))
+        flip = (1 << i) | (1 << j)
+        assert ((su ^ cu) == flip and sd == cd and spin in (-1, 0)) or \
+               ((sd ^ cd) == flip and su == cu and spin in (-1, 1))
+    # every nonzero off-diagonal element of H is listed exactly once
+    nz = [(a, b) for a, b in zip(*np.nonzero(Hk)) if a != b]
+    assert sorted(nz) == sorted(zip(rows.tolist(), cols.tolist()))
+
+
+def test_pattern_terms_spin_signs_are_positive_and_ids_follow_bonds():
+    terms = _random_spin_terms(8, 10, 21)
+    m = O.Model("SPIN_HALF", 8, 4, 0, terms)
+    rows, cols, signs, tids = m.pattern_terms(0, m.dim)
+    assert np.all(signs == 1)
+    for r, c, k in zip(rows[:500], cols[:500], tids[:500]):
+        _, i, j, _, _, _ = terms[k]
+        assert m.row_state(int(r))[0] ^ m.row_state(int(c))[0] == (1 << i) | (1 << j)

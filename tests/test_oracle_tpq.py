@@ -142,17 +142,64 @@ def test_mtpq_temperature_follows_the_canonical_energy():
                 assert abs(u_ - ec[0] / N) < 0.05, (k, u_, ec[0] / N)
 
 
-def test_binding_bootstrap_agrees_with_the_oracle():
-    """The binding's post-processing of cTPQ samples (E, C/beta^2 by the
-    paper's bootstrap) against the oracle's, on random sample data."""
-    import numpy as np
-    import oracle as O
-    from paper_2307_13222_gb300.hphi import tpq_thermo
-    rng = np.random.default_rng(3)
-    e = rng.normal(size=(12, 30))
-    h2 = e * e + rng.random(size=(12, 30))
-    ln = np.cumsum(rng.normal(scale=0.1, size=(12, 30)), axis=1)
-    (hm, hs), (fm, fs) = tpq_thermo(e, h2, ln, P=12, M=6, seed=5)
-    bs = O.bootstrap_tpq(e, h2, ln, P=12, M=6, seed=5)
-    assert np.allclose(hm, bs["H"][0], rtol=1e-12) and np.allclose(hs, bs["H"][1], rtol=1e-12)
-    assert np.allclose(fm, bs["fluct"][0], rtol=1e-12) and np.allclose(fs, bs["fluct"][1], rtol=1e-12)
+def _two_sample_set():
+    """Two samples at one temperature: weights 1 and 3 (log norms 0, log 3),
+    <H> = 1, 2 and <H^2> = 2, 5."""
+    num_h = np.array([[1.0], [2.0]])
+    num_h2 = np.array([[2.0], [5.0]])
+    logn = np.array([[0.0], [math.log(3.0)]])
+    return num_h, num_h2, logn
+
+
+def test_bootstrap_sigma_over_every_resampling_by_hand():
+    """All four ordered resamplings of P = 2 from N = 2 (with replacement),
+    passed explicitly.  Per resampling <H>_m = sum w H / sum w:
+      (0,0): 1,  (0,1), (1,0): (1 + 3*2)/4 = 7/4,  (1,1): 2;
+    mean 13/8, squared deviations 25/64, 1/64, 1/64, 9/64 (sum 9/16), so
+    sigma^2 = (9/16)/(M-1) = 3/16 (a 1/M divisor gives 9/64).
+    <H^2>_m: 2, 17/4, 17/4, 5;  fluctuation <H^2>_m - <H>_m^2: 1, 19/16, 19/16, 1;
+    mean 35/32, squared deviations 4 x 9/1024, sigma^2 = (36/1024)/3 = 3/256."""
+    num_h, num_h2, logn = _two_sample_set()
+    picks = np.array([[0, 0], [0, 1], [1, 0], [1, 1]])
+    bs = O.bootstrap_tpq(num_h, num_h2, logn, P=2, M=4, picks=picks)
+    mean, sd = bs["H"]
+    assert mean[0] == pytest.approx(13 / 8, rel=1e-15)
+    assert sd[0] == pytest.approx(math.sqrt(3 / 16), rel=1e-14)
+    assert sd[0] != pytest.approx(math.sqrt(9 / 64), rel=1e-3)
+    fm, fsd = bs["fluct"]
+    assert fm[0] == pytest.approx(35 / 32, rel=1e-15)
+    assert fsd[0] == pytest.approx(math.sqrt(3 / 256), rel=1e-13)
+    h2m, h2sd = bs["H2"]
+    assert h2m[0] == pytest.approx((2 + 17 / 4 + 17 / 4 + 5) / 4, rel=1e-15)
+
+
+def test_bootstrap_sample_zero_normalisation_cancels():
+    """Dividing every norm by sample 0's (the paper's W) changes nothing:
+    shifting all log norms of a temperature by a constant leaves the result."""
+    num_h, num_h2, logn = _two_sample_set()
+    picks = np.array([[0, 1], [1, 1], [0, 0]])
+    a = O.bootstrap_tpq(num_h, num_h2, logn, P=2, M=3, picks=picks)
+    b = O.bootstrap_tpq(num_h, num_h2, logn + 40.0, P=2, M=3, picks=picks)
+    for k in ("H", "H2", "fluct"):
+        assert np.allclose(a[k][0], b[k][0], rtol=1e-14) and np.allclose(a[k][1], b[k][1], rtol=1e-12)
+
+
+def test_bootstrap_draws_are_uniform_with_replacement():
+    """The seeded resamplings draw with replacement: for N = P = 2 half of the
+    resamplings repeat an index (none would without replacement), and every
+    index is equally likely."""
+    from workloads import bootstrap_picks
+    M = 20000
+    picks = bootstrap_picks(M, 2, 2, seed=7)
+    rep = np.mean(picks[:, 0] == picks[:, 1])
+    assert abs(rep - 0.5) < 4 * math.sqrt(0.25 / M)
+    p10 = bootstrap_picks(4000, 25, 10, seed=8)
+    counts = np.bincount(p10.reshape(-1), minlength=10)
+    n = p10.size
+    assert p10.min() == 0 and p10.max() == 9
+    assert np.all(np.abs(counts / n - 0.1) < 4 * math.sqrt(0.09 / n))
+    # the seeded path of the oracle uses exactly these picks
+    num_h, num_h2, logn = _two_sample_set()
+    a = O.bootstrap_tpq(num_h, num_h2, logn, P=2, M=50, seed=3)
+    b = O.bootstrap_tpq(num_h, num_h2, logn, P=2, M=50, picks=bootstrap_picks(50, 2, 2, 3))
+    assert np.array_equal(a["H"][1], b["H"][1])

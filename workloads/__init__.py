@@ -8,11 +8,11 @@ the other.
 """
 from .lattice import chain, ladder, square, random_regular_graph, splitmix64_stream, uniform_couplings
 from .terms import heisenberg_terms, xxz_terms, hubbard_terms, TERM_KINDS
-from .rng import philox4x32_10, philox_uniform53, philox_gaussian, random_vectors
+from .rng import philox4x32_10, philox_uniform53, philox_gaussian, random_vectors, bootstrap_picks
 from . import configs
 
 __all__ = [
     "chain", "ladder", "square", "random_regular_graph", "splitmix64_stream", "uniform_couplings",
     "heisenberg_terms", "xxz_terms", "hubbard_terms", "TERM_KINDS",
-    "philox4x32_10", "philox_uniform53", "philox_gaussian", "random_vectors", "configs",
+    "philox4x32_10", "philox_uniform53", "philox_gaussian", "random_vectors", "bootstrap_picks", "configs",
 ]

@@ -78,3 +78,15 @@ def random_vectors(rows: int, cols: int, seed: int, complex_: bool = False,
     if normalize:
         out /= np.linalg.norm(out, axis=0, keepdims=True)
     return out
+
+
+def bootstrap_picks(M: int, P: int, n_samples: int, seed: int) -> np.ndarray:
+    """[M][P] sample indices drawn uniformly with replacement from
+    0 .. n_samples-1: pick e = m * P + p is floor(U * n_samples) (capped at
+    n_samples - 1) with U the 53-bit uniform of output words (0, 1) of the
+    Philox stream element e under key `seed` (the resamplings of the TPQ
+    bootstrap)."""
+    w0, w1, _, _ = _words(0, M * P, seed)
+    u = philox_uniform53(w0, w1)
+    k = np.floor(u * n_samples).astype(np.int64)
+    return np.minimum(k, n_samples - 1).reshape(M, P)
