@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhphi.so")
-SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "hv_seg.cu", "vec.cu", "pattern.cu", "capi.cu", "drivers.cu",
+SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "hv_seg.cu", "hv_tile.cu", "vec.cu", "pattern.cu", "capi.cu", "drivers.cu",
            "spectrum.cu", "evolve.cu", "batch.cu", "serve.cu",
            "lobpcg.cu", "tune.cu", "methods.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,7 +41,7 @@ def _stale() -> bool:
 
 
 # sources that decide the code and tables of the H*x kernels
-HV_SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "hv_seg.cu",
+HV_SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "hv_seg.cu", "hv_tile.cu",
               "hvcommon.cuh", "rowvisit.cuh", "hphi_internal.cuh"]
 
 

@@ -143,9 +143,10 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->ph_off);
     cudaFree(h->dterms_d);
     cudaFree(h->rowstate);
-    cudaFree(h->seg_r8);
-    cudaFree(h->seg_un);
     cudaFree(h->seg_so);
+    cudaFree(h->tile_tab);
+    cudaFree(h->tile_diag);
+    delete h->tile;
     delete h->seg;
     delete h;
 }

@@ -71,6 +71,17 @@ struct DTerm {
     double a, b;        // spin: Jz, Jxy; hop: t; U: U; V: V
 };
 
+// Tiled two-pass block H*V (hv_tile.cu): per pass the bit set of the tile's
+// rows (nin bits varied inside a tile, nout bits fixed per tile), its bonds
+// (masks and Jxy/2), and the bit-deposit tables of both index parts.
+constexpr int kTileMaxBonds = 64;
+struct TileArgs {
+    const uint32_t *tab;  // [2 passes][inner, outer][4 bytes][256]
+    int nin[2], nout[2], nb[2];
+    uint32_t m[2][kTileMaxBonds];
+    double c[2][kTileMaxBonds];
+};
+
 // Per-Hamiltonian descriptor (device copy read by every block at set-up).
 struct HamDesc {
     int model;
@@ -89,23 +100,12 @@ struct HamDesc {
     double coef[kMaxCoef];
 };
 
-// Segment H*x kernel (hv_seg.cu): bond classes by where the two sites lie
-// (l0 = the lowest min(8, N_lo) bits of the low half, l1 = the rest of it,
-// h = the high half), the n0-bit rank tables and the segment offsets SO.
-constexpr int kSegMax = 32;  // bonds per class
+// High-high pass (hv_seg.cu): the low half split into its lowest n0 =
+// min(8, N_lo) bits and the upper n1 = N_lo - n0 bits l1, and the segment
+// offsets SO[p][l1] = number of class-p low halves whose upper part is below l1.
 struct SegArgs {
     int n0, n1, nlo, nhi, n;
-    int nA, nB, nC, nE, nF;
-    uint8_t A0[kSegMax], A1[kSegMax];  // A: l0 bits i < j
-    uint8_t B0[kSegMax], B1[kSegMax];  // B: l0 bit i, l1 bit b
-    uint8_t C0[kSegMax], C1[kSegMax];  // C: l1 bits
-    uint8_t E0[kSegMax], E1[kSegMax];  // E: l0 bit i, h bit a
-    uint8_t F0[kSegMax], F1[kSegMax];  // F: l1 bit b, h bit a
-    double cA[kSegMax], cB[kSegMax], cC[kSegMax], cE[kSegMax], cF[kSegMax];  // Jxy / 2
-    uint16_t off8[10];  // first position of each popcount class in un8
-    const uint8_t *r8;  // [2^n0] rank of an n0-bit string within its popcount class
-    const uint8_t *un8; // [2^n0] the n0-bit strings ordered by (popcount, value)
-    const uint16_t *so; // [(N_lo + 1) << n1] SO[p][l1]
+    const uint16_t *so;  // [(N_lo + 1) << n1]
 };
 
 // Lin tables of one species (spin string, or up / down fermion string).
@@ -139,7 +139,7 @@ struct hphi_ctx {
     void *vec[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t vec_bytes = 0;
     int *dflag = nullptr;        // device status word of consistency checks
-    // segment H*x: the first pass's partial products when y cannot hold them
+    // high-high pass: its partial products when y cannot hold them
     void *seg_tmp = nullptr;
     size_t seg_tmp_bytes = 0;
     // streaming H*x on host vectors: two x and two y device buffers, copy
@@ -195,11 +195,15 @@ struct hphi_ham {
     int32_t *ph_off = nullptr;
     int64_t ph_mx0 = 0;          // first offset row of the mixed-bond groups
     int max_row_entries = 0;
-    // segment kernel (spin S^z sector, N_lo <= 16): host copy of its
-    // arguments (null when not available) and its device tables
+    // high-high pass (spin S^z sector, N_lo <= 16): host copy of its
+    // arguments (null when not available) and its device table
     hphi::SegArgs *seg = nullptr;
-    uint8_t *seg_r8 = nullptr, *seg_un = nullptr;
     uint16_t *seg_so = nullptr;
+    // tiled block kernel (full space, 32 FP32 columns): built on first use
+    hphi::TileArgs *tile = nullptr;
+    int tile_tried = 0;
+    uint32_t *tile_tab = nullptr;
+    float *tile_diag = nullptr;  // the diagonal of H, one FP32 value per row
     // plain term list (host and device) and, for the S^z sector, the state of
     // every row (built on first use by the small-problem solver)
     std::vector<hphi::DTerm> dterms;
@@ -308,8 +312,10 @@ int lowest_ritz(int m, const double *alpha, const double *beta2, double *theta, 
 // the same with a warm start (an upper bound of the lowest eigenvalue, updated)
 int lowest_ritz_warm(int m, const double *alpha, const double *beta2, double *warm, double *theta, double *ylast);
 
-// ---- segment H*x tables (hv_seg.cu) -------------------------------------------------
+// ---- high-high pass table (hv_seg.cu) ------------------------------------------------
 int build_seg_tables(hphi_ctx *ctx, hphi_ham *H);
+// ---- tiled block kernel tables (hv_tile.cu) ------------------------------------------
+int build_tile_tables(hphi_ctx *ctx, hphi_ham *H);
 
 // ---- pattern (pattern.cu) --------------------------------------------------------
 int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,

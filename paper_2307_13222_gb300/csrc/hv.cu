@@ -305,8 +305,10 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         // (measured faster than the table-driven kernel on the 6x5 and 4x8 sectors)
         const bool one_col = same_ld && red_mode >= 0 && L.ldx == 1 && L.ncol == 1 && !L.swap &&
                              (double)ham->D < 4294967296.0;
-        // the segment kernel (variant 4): spin sector, one column, rows addressed with 32-bit offsets
-        const bool seg = ham->tune_variant == 4 && ham->seg && one_col && (double)ham->D < 2147483648.0;
+        // the high-high pass plus the bond-major kernel (variant 4): spin sector, one column,
+        // row offsets of 32 bits
+        const bool seg = ham->tune_variant == 4 && ham->seg && ham->ph_ent && ham->host.n_ll <= 128 && one_col &&
+                         (double)ham->D < 2147483648.0;
         const bool spin_staged = !seg &&
                                  (ham->tune_variant == 2 || ham->tune_variant == 3 || ham->tune_variant < 0) &&
                                  ham->model == HPHI_SPIN_HALF && ham->nlo <= 16 && ham->host.n_ll <= 128 && one_col;
@@ -376,9 +378,35 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         for (int r = 0; r < 3; r++) a.red[r] = L.red[r];
         a.partials = L.partials ? L.partials + part_off : nullptr;
         a.swap = L.swap;
+        a.tin = nullptr;
         if (L.swap && ((nc % 2) != 0 || (c0 % 2) != 0 || (fG == 1 && fcpl == 1) || (cpl == 1)))
             return set_err(ctx, HPHI_E_INVAL, "pair swap: column slice [%d, %d) splits a pair", c0, c0 + nc);
         int grid = 0, st;
+        // the tiled two-pass block kernel (variant 5): full space, 32 FP32 columns, 16-byte rows
+        bool tiled = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (ham->tune_variant == 5 && ham->model == HPHI_SPIN_HALF_GC && c0 == 0 && L.ncol == 32 &&
+                L.ldx == 32 && L.ldy == 32 && (!L.v || L.ldv == 32) && red_mode >= 0 && aligned(xs, 16) &&
+                aligned(ys, 16) && aligned(vs, 16)) {
+                if ((st = build_tile_tables(ctx, const_cast<hphi_ham *>(ham)))) return st;
+                tiled = ham->tile != nullptr;
+            }
+        }
+        if (tiled) {
+            a.ncol = 32;
+            for (int c = 0; c < 32; c++) {
+                a.alpha[c] = L.alpha_h ? L.alpha_h[c] : L.alpha_s;
+                a.gamma[c] = L.gamma_h ? L.gamma_h[c] : L.gamma_s;
+            }
+            if constexpr (std::is_same<T, float>::value) st = launch_tile(ctx, ham, a, red_mode, &grid);
+            if (st) return st;
+            L.sgrid[L.nslice] = grid;
+            L.sc0[L.nslice] = 0;
+            L.snc[L.nslice] = 32;
+            L.nslice++;
+            c0 = 32;
+            continue;
+        }
         if (staged) {
             set_traversal(ctx, ham, a.P, (double)sizeof(T));
             a.P.split = 1;
@@ -477,7 +505,7 @@ extern "C" int hphi_ham_set_tuning(hphi_ham *ham, int knob, int value) {
         ham->tune_hints = value;
         return HPHI_OK;
     case HPHI_TUNE_VARIANT:
-        if (value < -1 || value > 4) return HPHI_E_INVAL;
+        if (value < -1 || value > 5) return HPHI_E_INVAL;
         ham->tune_variant = value;
         return HPHI_OK;
     case HPHI_TUNE_COOP:

@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
         const uint32_t q0 = (uint32_t)(((uint64_t)len * (uint32_t)(warp * RPW)) / kPhRanges);
         const uint32_t q1 = (uint32_t)(((uint64_t)len * (uint32_t)((warp + 1) * RPW)) / kPhRanges);
         // 1. diagonal and high-high bonds, two rows per lane at a time (twice the
-        // gathers in flight)
-        const int nhh = hb.nhh;
+        // gathers in flight); with a.tin the high-high terms come precomputed
+        const int nhh = a.tin ? 0 : hb.nhh;
         for (uint32_t q = q0 + lane; q < q1; q += 64) {
             const bool two = q + 32 < q1;
             T acc[2];
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
                     const uint32_t l = hub ? __ldg(P.states_dn + qq) : __ldg(P.lstate + cp);
                     T d = __ldg(dlow + cp) + hb.dh;
                     for (int g = 0; g < P.ngroups; g++) d += hb.tab[g][(l >> (8 * g)) & 255u];
-                    acc[t] = d * xs[qq];
+                    acc[t] = a.tin ? fma(d, xs[qq], a.tin[base + qq]) : d * xs[qq];
                 }
             }
             for (int k0 = 0; k0 < nhh; k0 += kPhGathers) {

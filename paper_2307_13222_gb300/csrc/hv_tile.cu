@@ -1,0 +1,415 @@
+// Tiled two-pass block H*V for spin-1/2 models on the full 2^N space, 32 real
+// columns in FP32 (16 complex columns: the cTPQ block of Sec. 3.5.2 and the
+// real-time evolution of Sec. 3.4).
+//
+// Row s (an N-bit spin string) holds 32 columns, 128 contiguous bytes.  An
+// exchange bond (i, j) with Jxy != 0 couples s with s ^ (2^i | 2^j) where the
+// two bits differ (Sec. 3.1.1).  The single-pass kernels gather about 20 such
+// rows per row from all over the 8.6 GB block and move about 6x the
+// algorithmic bytes from DRAM.
+//
+// Here the off-diagonal bonds are split over two passes.  Pass k works on a
+// bit set S_k: it walks the rows tile by tile, a tile being the 2^|S_k| rows
+// that share the bits outside S_k, every thread block on the same tile at a
+// time, and applies only bonds with both sites in S_k, so every gather stays
+// inside the current tile, which is sized to a fraction of L2 and comes from
+// DRAM once.  The sets come from the bond graph: A and B disjoint site sets
+// with no bond between them, S_1 = all sites but A, S_2 = all sites but B;
+// a bond touching A lies in S_2, one touching B in S_1, the rest in both
+// (split for balance).  So each pass reads x once and the pair moves
+//   pass 1: x, diagonal (4 B per row), t written;
+//   pass 2: x, t, v (the gamma term), y written
+// instead of x about 17 times.
+//   pass 1:  t[s] = d[s] x[s] + sum_{bonds of pass 1} c_b x[s ^ m_b]
+//   pass 2:  acc = t[s] + sum_{bonds of pass 2} c_b x[s ^ m_b],
+//            y = alpha acc + beta y + gamma v  (pair swap, fused reductions)
+// d is the diagonal, sum_b Jz_b S^z_i S^z_j, stored once per Hamiltonian as
+// an FP32 vector.  t lives in y when y's old value is not read (beta = 0 and
+// v != y), else in a context buffer.  Lanes: 8 per row, 4 columns (16 bytes)
+// each; 4 rows per warp.  Every row sums its terms in a fixed order
+// (ascending bond index): deterministic.
+#include "hvcommon.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace hphi {
+
+namespace {
+
+constexpr int kTileThreads = 256;
+constexpr int kTileItemBits = 5;  // 32 rows (4 per warp) per thread-block iteration
+
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void ldc4(const float *p, float (&v)[4]) {  // coherent: may alias y
+    asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
+
+__global__ void k_tile_diag(const DTerm *terms, int nt, int64_t D, float *d) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < D; s += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < nt; k++) {
+            const DTerm &t = terms[k];
+            if (t.kind != DT_SPIN) continue;
+            v += (((s >> t.i) ^ (s >> t.j)) & 1) ? -0.25 * t.a : 0.25 * t.a;
+        }
+        d[s] = (float)v;
+    }
+}
+
+// One pass.  PASS 1 writes t; PASS 2 reads t and applies the epilogue.
+// Eight lanes per row, four columns (16 bytes) each; four rows per warp;
+// four bonds (tested, their targets loaded) in flight.
+template <int PASS, int RED>
+__global__ void __launch_bounds__(kTileThreads, (PASS == 1 || RED == 0) ? 4 : 3)
+    k_tile(const HvArgs<float> a, const TileArgs ta, const float *__restrict__ diag, float *tbuf) {
+    __shared__ uint32_t pin[4][256], pout[4][256];
+    __shared__ uint32_t bm[kTileMaxBonds];
+    __shared__ float bc[kTileMaxBonds];
+    constexpr int P = PASS - 1;
+    const uint32_t *tab = ta.tab + (size_t)P * 8 * 256;
+    for (int i = threadIdx.x; i < 4 * 256; i += kTileThreads) {
+        pin[i >> 8][i & 255] = tab[i];
+        pout[i >> 8][i & 255] = tab[4 * 256 + i];
+    }
+    const int nb = ta.nb[P];
+    for (int i = threadIdx.x; i < nb; i += kTileThreads) {
+        bm[i] = ta.m[P][i];
+        bc[i] = (float)ta.c[P][i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane & 7, rsub = lane >> 3;
+    const int nin = ta.nin[P];
+    const int64_t per_tile = (int64_t)1 << (nin - kTileItemBits);
+    const int64_t items = per_tile << ta.nout[P];
+    const float *__restrict__ X = a.x;
+    float al[4], ga[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        al[k] = (float)(a.alpha_dev ? a.alpha_dev[4 * gl + k] : a.alpha[4 * gl + k]);
+        ga[k] = (float)(a.gamma_dev ? a.gamma_dev[4 * gl + k] : a.gamma[4 * gl + k]);
+    }
+    const float be = (float)a.beta;
+    const bool use_beta = a.beta != 0.0, use_v = a.v != nullptr;
+    constexpr int NR = RED == 2 ? 3 : (RED ? 1 : 0);
+    RedAcc<float> racc[NR > 0 ? NR : 1][4];
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        const uint32_t t = (uint32_t)(w >> (nin - kTileItemBits));
+        const uint32_t inner = ((uint32_t)(w & (per_tile - 1)) << kTileItemBits) | (uint32_t)(warp * 4 + rsub);
+        const uint32_t s = pin[0][inner & 255] | pin[1][(inner >> 8) & 255] | pin[2][(inner >> 16) & 255] |
+                           pin[3][inner >> 24] | pout[0][t & 255] | pout[1][(t >> 8) & 255] |
+                           pout[2][(t >> 16) & 255] | pout[3][t >> 24];
+        const uint64_t roff = (uint64_t)s * 32 + 4 * gl;
+        float acc[4], xo[4];
+        if constexpr (PASS == 1) {
+            ld4(X + roff, xo);
+            const float d = __ldg(diag + s);
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[k] = d * xo[k];
+        } else {
+            ldc4(tbuf + roff, acc);
+        }
+        int k = 0;
+        for (; k + 4 <= nb; k += 4) {
+            float v[4][4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t m = bm[k + u];
+                ok[u] = __popc(s & m) == 1;
+                if (ok[u]) ld4(X + (uint64_t)(s ^ m) * 32 + 4 * gl, v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (ok[u]) {
+                    const float c = bc[k + u];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[j] = fmaf(c, v[u][j], acc[j]);
+                }
+        }
+        for (; k < nb; k++) {
+            const uint32_t m = bm[k];
+            if (__popc(s & m) == 1) {
+                float v[4];
+                ld4(X + (uint64_t)(s ^ m) * 32 + 4 * gl, v);
+                const float c = bc[k];
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[j] = fmaf(c, v[j], acc[j]);
+            }
+        }
+        if constexpr (PASS == 1) {
+            st4(tbuf + roff, acc);
+        } else {
+            float out[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) out[j] = al[j] * (a.swap ? acc[j ^ 1] : acc[j]);
+            float *yr = a.y + roff;
+            if (use_beta) {
+                float yo[4];
+                ldc4(yr, yo);
+#pragma unroll
+                for (int j = 0; j < 4; j++) out[j] = fmaf(be, yo[j], out[j]);
+            }
+            if (use_v) {
+                float vo[4];
+                ldc4(a.v + roff, vo);
+#pragma unroll
+                for (int j = 0; j < 4; j++) out[j] = fmaf(ga[j], vo[j], out[j]);
+            }
+            st4(yr, out);
+            if constexpr (RED == 1 || RED == 2) ld4(X + roff, xo);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if constexpr (RED == 1) racc[0][j].add(xo[j], out[j]);
+                if constexpr (RED == 2) {
+                    racc[0][j].add(xo[j], acc[j]);
+                    racc[1][j].add(acc[j], acc[j]);
+                    racc[2][j].add(xo[j], xo[j]);
+                }
+                if constexpr (RED == 3) racc[0][j].add(out[j], out[j]);
+            }
+        }
+    }
+    if constexpr (PASS == 2 && RED != 0) {
+        // lanes gl, gl + 8, gl + 16, gl + 24 hold the same columns
+        __shared__ double red_sm[kTileThreads / 32][3][32];
+#pragma unroll
+        for (int r = 0; r < NR; r++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                double v = racc[r][j].value();
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (rsub == 0) red_sm[warp][r][4 * gl + j] = v;
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * 32; i += kTileThreads) {
+            const int r = i / 32, c = i % 32;
+            double sum = 0.0;
+            if (r < NR)
+                for (int w2 = 0; w2 < kTileThreads / 32; w2++) sum += red_sm[w2][r][c];
+            a.partials[((int64_t)blockIdx.x * 3 + r) * a.ncol + c] = sum;
+        }
+    }
+}
+
+uint32_t pdep32(uint32_t v, uint32_t mask) {
+    uint32_t out = 0;
+    for (int b = 0; b < 32 && v; b++)
+        if ((mask >> b) & 1u) {
+            if (v & 1u) out |= 1u << b;
+            v >>= 1;
+        }
+    return out;
+}
+
+// Two disjoint site sets A, B with no off-diagonal bond between them and
+// N - |A|, N - |B| <= smax: A grown greedily from each start site by the
+// neighbour that adds the fewest new neighbours, B taken from the sites
+// neither in A nor next to it.  Returns false when no start site gives both
+// sizes.
+bool find_cover(int N, const std::vector<uint64_t> &adj, int smax, uint64_t *A_out, uint64_t *B_out) {
+    const int need = N - smax;
+    if (need <= 0) {
+        *A_out = 0;
+        *B_out = 0;
+        return true;
+    }
+    const uint64_t all = N == 64 ? ~0ull : ((1ull << N) - 1);
+    auto nbr = [&](uint64_t A) {
+        uint64_t n = 0;
+        for (int v = 0; v < N; v++)
+            if ((A >> v) & 1) n |= adj[v];
+        return n & ~A;
+    };
+    for (int st = 0; st < N; st++) {
+        uint64_t A = 1ull << st;
+        while (__builtin_popcountll(A) < need) {
+            const uint64_t cand = nbr(A) ? nbr(A) : (all & ~A);
+            int best = -1, bc = 1 << 30;
+            for (int v = 0; v < N; v++) {
+                if (!((cand >> v) & 1)) continue;
+                const int c = __builtin_popcountll(nbr(A | (1ull << v)));
+                if (c < bc) {
+                    bc = c;
+                    best = v;
+                }
+            }
+            if (best < 0) break;
+            A |= 1ull << best;
+            const uint64_t R = all & ~(A | nbr(A));
+            if (__builtin_popcountll(A) >= need && __builtin_popcountll(R) >= need) {
+                // B: `need` sites of R (the fewest that bring pass 2 within smax;
+                // the sites left out keep their bonds free for either pass)
+                uint64_t B = 0;
+                for (int v = 0; v < N && __builtin_popcountll(B) < need; v++)
+                    if ((R >> v) & 1) B |= 1ull << v;
+                *A_out = A;
+                *B_out = B;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+template <int PASS>
+int go_tile(hphi_ctx *ctx, const HvArgs<float> &a, const TileArgs &ta, const float *diag, float *tbuf, int red_mode,
+            int grid) {
+#define HPHI_TILE(R) k_tile<PASS, R><<<grid, kTileThreads, 0, ctx->stream>>>(a, ta, diag, tbuf)
+    switch (red_mode) {
+    case 0: HPHI_TILE(0); break;
+    case 1: HPHI_TILE(1); break;
+    case 2: HPHI_TILE(2); break;
+    case 3: HPHI_TILE(3); break;
+    default: return HPHI_E_INVAL;
+    }
+#undef HPHI_TILE
+    HPHI_CUDA(ctx, cudaGetLastError());
+    return HPHI_OK;
+}
+
+}  // namespace
+
+// Bit sets, bond split and tables of the tiled kernel for a full-space spin
+// Hamiltonian (built on the first launch that asks for it).  Leaves
+// ham->tile null when the model is not eligible or no split fits L2.
+int build_tile_tables(hphi_ctx *ctx, hphi_ham *H) {
+    if (H->tile || H->tile_tried) return HPHI_OK;
+    H->tile_tried = 1;
+    if (H->model != HPHI_SPIN_HALF_GC) return HPHI_OK;
+    const int N = H->basis->N;
+    if (N < kTileItemBits || N > 32) return HPHI_OK;
+    std::vector<uint64_t> adj(N, 0);
+    struct Bd {
+        int i, j;
+        double c;
+    };
+    std::vector<Bd> bonds;
+    for (const DTerm &t : H->dterms) {
+        if (t.kind != DT_SPIN || t.b == 0.0) continue;
+        adj[t.i] |= 1ull << t.j;
+        adj[t.j] |= 1ull << t.i;
+        bonds.push_back(Bd{t.i, t.j, 0.5 * t.b});
+    }
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess || l2 <= 0) {
+        cudaGetLastError();
+        return HPHI_OK;
+    }
+    // a tile of 2^s rows x 128 bytes within 30 % of L2
+    int smax = kTileItemBits;
+    while (smax < N && ((double)128 * (double)(2ull << smax)) <= 0.3 * (double)l2) smax++;
+    uint64_t A = 0, B = 0;
+    if (!find_cover(N, adj, smax, &A, &B)) return HPHI_OK;
+    const uint64_t all = (N == 64) ? ~0ull : ((1ull << N) - 1);
+    TileArgs ta{};
+    const uint64_t S[2] = {all & ~A, all & ~B};
+    std::vector<Bd> part[2];
+    for (const Bd &b : bonds) {
+        const uint64_t m = (1ull << b.i) | (1ull << b.j);
+        const bool in1 = (m & A) == 0, in2 = (m & B) == 0;
+        if (in1 && in2) part[part[0].size() <= part[1].size() ? 0 : 1].push_back(b);
+        else if (in1) part[0].push_back(b);
+        else part[1].push_back(b);
+    }
+    std::vector<uint32_t> tab(2 * 8 * 256);
+    for (int p = 0; p < 2; p++) {
+        if ((int)part[p].size() > kTileMaxBonds) return HPHI_OK;
+        ta.nin[p] = __builtin_popcountll(S[p]);
+        ta.nout[p] = N - ta.nin[p];
+        if (ta.nin[p] < kTileItemBits) return HPHI_OK;
+        ta.nb[p] = (int)part[p].size();
+        for (size_t k = 0; k < part[p].size(); k++) {
+            ta.m[p][k] = (1u << part[p][k].i) | (1u << part[p][k].j);
+            ta.c[p][k] = part[p][k].c;
+        }
+        const uint32_t in_mask = (uint32_t)S[p], out_mask = (uint32_t)(all & ~S[p]);
+        for (int byte = 0; byte < 4; byte++)
+            for (uint32_t v = 0; v < 256; v++) {
+                tab[(size_t)p * 2048 + byte * 256 + v] = pdep32(v << (8 * byte), in_mask);
+                tab[(size_t)p * 2048 + 1024 + byte * 256 + v] = pdep32(v << (8 * byte), out_mask);
+            }
+    }
+    const int64_t D = H->D;
+    cudaError_t e = cudaMalloc((void **)&H->tile_tab, tab.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(H->tile_tab, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&H->tile_diag, (size_t)D * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(H->tile_tab);
+        H->tile_tab = nullptr;
+        return cuda_err(ctx, e, "tiled kernel tables");
+    }
+    k_tile_diag<<<(int)std::min<int64_t>((D + 255) / 256, (int64_t)ctx->sm_count * 16), 256, 0, ctx->stream>>>(
+        H->dterms_d, (int)H->dterms.size(), D, H->tile_diag);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "tiled kernel diagonal");
+    ta.tab = H->tile_tab;
+    H->tile = new (std::nothrow) TileArgs(ta);
+    if (!H->tile) return set_err(ctx, HPHI_E_NOMEM, "tiled kernel tables");
+    return HPHI_OK;
+}
+
+int launch_tile(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<float> &a, int red_mode, int *grid) {
+    if (!ham->tile) return set_err(ctx, HPHI_E_INVAL, "tiled H*V: not available for this Hamiltonian");
+    const TileArgs &ta = *ham->tile;
+    const size_t need = (size_t)ham->D * 32 * sizeof(float);
+    float *tbuf = nullptr;
+    if (a.beta == 0.0 && (a.v == nullptr || a.v != a.y)) {
+        tbuf = a.y;
+    } else {
+        if (ctx->seg_tmp_bytes < need) {
+            HPHI_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(ctx->seg_tmp);
+            ctx->seg_tmp = nullptr;
+            ctx->seg_tmp_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->seg_tmp, need);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "tiled H*V buffer");
+            ctx->seg_tmp_bytes = need;
+        }
+        tbuf = (float *)ctx->seg_tmp;
+    }
+    static int occ1[64] = {0}, occ2[64][4] = {{0}};
+    const int dev = ctx->device;
+    if (occ1[dev] == 0) {
+        auto occ_of = [](const void *f) {
+            int n = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kTileThreads, 0);
+            return n > 0 ? n : 1;
+        };
+        occ1[dev] = occ_of((const void *)k_tile<1, 0>);
+        occ2[dev][0] = occ_of((const void *)k_tile<2, 0>);
+        occ2[dev][1] = occ_of((const void *)k_tile<2, 1>);
+        occ2[dev][2] = occ_of((const void *)k_tile<2, 2>);
+        occ2[dev][3] = occ_of((const void *)k_tile<2, 3>);
+    }
+    if (red_mode < 0 || red_mode > 3) return set_err(ctx, HPHI_E_INVAL, "tiled H*V: unknown reduction mode");
+    // no more thread blocks than the partials of an H*x launch hold (8 per SM)
+    auto grid_of = [&](int occ) {
+        int64_t g = (int64_t)(occ < 8 ? occ : 8) * ctx->sm_count;
+        if (g > ham->nh) g = ham->nh;
+        return (int)(g < 1 ? 1 : g);
+    };
+    const int g1 = grid_of(occ1[dev]), g2 = grid_of(occ2[dev][red_mode]);
+    *grid = g2;
+    const int slot = prof_begin(ctx, PROF_HV);
+    int st = go_tile<1>(ctx, a, ta, ham->tile_diag, tbuf, 0, g1);
+    if (!st) st = go_tile<2>(ctx, a, ta, ham->tile_diag, tbuf, red_mode, g2);
+    prof_end(ctx, slot);
+    if (st) return st;
+    snprintf(ctx->last_kernel, sizeof ctx->last_kernel, "k_tile<f32,RED%d>x2@" HPHI_SRC_TAG, red_mode);
+    return HPHI_OK;
+}
+
+}  // namespace hphi

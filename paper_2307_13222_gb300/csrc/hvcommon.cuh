@@ -98,6 +98,8 @@ struct HvArgs {
     int red[3];
     double *partials;  // [grid][3][ncol]
     int swap;          // out[c] takes (H x)[c ^ 1]: multiplication by -i / +i of complex columns
+    const T *tin;      // bond-major kernel: the high-high terms of every row, computed by a
+                       // separate pass (the kernel then skips its high-high phase); else null
 };
 
 inline HvTables make_tables(const hphi_ham *ham, int real_dtype) {
@@ -217,7 +219,9 @@ int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int re
 template <typename T>
 int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
 uint32_t staged_block_len(const hphi_ham *ham);
-// segment kernel (hv_seg.cu): spin sector, one column, two passes
+// tiled two-pass block kernel (hv_tile.cu): full space, 32 FP32 columns
+int launch_tile(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<float> &a, int red_mode, int *grid);
+// high-high pass plus the bond-major kernel (hv_seg.cu): spin sector, one column
 template <typename T>
 int launch_seg(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, int red_mode, int *grid);
 

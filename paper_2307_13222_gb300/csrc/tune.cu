@@ -55,12 +55,14 @@ extern "C" int hphi_ham_autotune(hphi_ctx *ctx, hphi_ham *ham, int dtype, int nv
     // candidate settings: variant x split x hints (x coop for 32-column rows, x form of the staged kernel)
     std::vector<std::vector<int>> cand;
     const bool spin = ham->model != HPHI_HUBBARD;
-    const std::vector<int> variants = spin ? std::vector<int>{0, 1, 2, 3} : std::vector<int>{-1, 0};
+    const std::vector<int> variants = spin ? std::vector<int>{0, 1, 2, 3, 4, 5} : std::vector<int>{-1, 0};
     for (int v : variants)
         for (int sp : {1, 2, 4})
             for (int hi : {0, 1}) {
                 // the staged kernels own a row block per thread block and take one column
-                if (v >= 2 && (sp != 1 || nr != 1)) continue;
+                if (v >= 2 && v <= 4 && (sp != 1 || nr != 1)) continue;
+                // the tiled kernel: 32-column rows of the full space, one launch form
+                if (v == 5 && (sp != 1 || nr != 32 || ham->model != HPHI_SPIN_HALF_GC)) continue;
                 const std::vector<int> coops =
                     (spin && nr == 32 && v == 1) ? std::vector<int>{0, 1, 2, 3, 4, 5} : std::vector<int>{-1};
                 const std::vector<int> forms = (v == 2) ? std::vector<int>{0, 1, 2, 3} : std::vector<int>{0};

@@ -317,11 +317,11 @@ def test_last_kernel_names_the_launch():
 @pytest.mark.parametrize("N,nup", [(2, 1), (5, 2), (9, 4), (12, 6), (13, 4), (17, 8), (20, 7), (22, 11), (24, 12)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_segment_kernel(N, nup, dtype):
-    """Two-pass segment kernel (spin sector, one column): low halves of 1 to
-    12 bits (l1 of 0 to 4 bits), every popcount class, random XXZ couplings
-    incl. zero Jxy, so every bond class (high-high, low-high on either part,
-    within and across the parts of the low half) with and without terms; the
-    accumulate form (beta != 0) takes the context buffer, the plain one y."""
+    """High-high pass plus bond-major kernel (variant 4; spin sector, one
+    column): low halves of 1 to 12 bits (0 to 4 bits above the lowest 8, so
+    one to 16 chunks), every popcount class, random XXZ couplings incl. zero
+    Jxy; the accumulate form (beta != 0) keeps the high-high terms in the
+    context buffer, the plain one in y."""
     rng = random.Random(N * 41 + nup)
     pairs = list(itertools.combinations(range(N), 2))
     pairs = rng.sample(pairs, min(len(pairs), 3 * N))
@@ -330,15 +330,14 @@ def test_segment_kernel(N, nup, dtype):
     m, b, h = pair("SPIN_HALF", N, nup, 0, terms)
     h.set_tuning(variant=4)
     _check(m, h, dtype, 1, alpha=0.8, beta=0.0, seed=N)
-    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<"), h.ctx.last_kernel()
+    assert h.ctx.last_kernel().startswith("k_hhs+k_hvp<"), h.ctx.last_kernel()
     _check(m, h, dtype, 1, alpha=-1.1, beta=0.35, seed=N + 1)
 
 
 @pytest.mark.parametrize("Lx,Ly", [(4, 4), (6, 4), (5, 5), (6, 5)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_segment_kernel_square_lattices(Lx, Ly, dtype):
-    """Periodic square lattices up to 30 sites (S^z = 0): the lattice bonds
-    fall into every class at the split the kernel takes."""
+    """Periodic square lattices up to 30 sites (S^z = 0) through variant 4."""
     N = Lx * Ly
     m, b, h = pair("SPIN_HALF", N, N // 2, 0, heisenberg_terms(square(Lx, Ly), 1.0))
     h.set_tuning(variant=4)
@@ -348,7 +347,7 @@ def test_segment_kernel_square_lattices(Lx, Ly, dtype):
         rng = np.random.default_rng(N)
         rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 300)])
         assert _sampled_rows(m, h, dtype, 1, rows, 60 + N) < (1e-15 if dtype == torch.float64 else 1e-6)
-    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<")
+    assert h.ctx.last_kernel().startswith("k_hhs+k_hvp<")
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -358,7 +357,7 @@ def test_segment_square_4x8_full_size_sampled(dtype):
     rng = np.random.default_rng(29)
     rows = np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, 400)])
     assert _sampled_rows(m, h, dtype, 1, rows, 63) < (1e-15 if dtype == torch.float64 else 1e-6)
-    assert h.ctx.last_kernel().startswith("k_sgs+k_sgb<")
+    assert h.ctx.last_kernel().startswith("k_hhs+k_hvp<")
 
 
 @pytest.mark.parametrize("variant", [3, 4])
@@ -376,3 +375,29 @@ def test_fused_reductions_one_column_sector(variant):
         eo, h2o, do = m.tpq_step(Vo, 0.05, 6)
         assert np.allclose(e, eo, rtol=1e-12) and np.allclose(h2, h2o, rtol=1e-12)
         assert np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("N,seed", [(12, 9), (20, 3), (22, 4)])
+def test_tiled_block_kernel(N, seed):
+    """Tiled two-pass block kernel (variant 5; full space, 32 FP32 columns):
+    one tile holding every row (N = 12) and two passes over tiles of the
+    bond-graph split (N = 20, 22), plain and with the accumulate term."""
+    bonds = random_regular_graph(N, 3, seed)
+    m, b, h = pair("SPIN_HALF_GC", N, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, seed + 7)))
+    h.set_tuning(variant=5)
+    _check(m, h, torch.float32, 32, alpha=1.1, beta=0.0, seed=30 + N)
+    assert h.ctx.last_kernel().startswith("k_tile<f32,"), h.ctx.last_kernel()
+    _check(m, h, torch.float32, 32, alpha=-0.6, beta=0.25, seed=31 + N)
+
+
+def test_tiled_block_rrg26_full_size_sampled():
+    """The cTPQ block shape at full size (2^26 rows x 16 complex FP32 columns)
+    through the tiled kernel: two passes with 2^18- and 2^15-row tiles."""
+    bonds = random_regular_graph(26, 3, 4)
+    terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 1004))
+    m, b, h = pair("SPIN_HALF_GC", 26, 0, 0, terms)
+    h.set_tuning(variant=5)
+    rng = np.random.default_rng(11)
+    rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 200)])
+    assert _sampled_rows(m, h, torch.float32, 32, rows, 45) < 1e-6
+    assert h.ctx.last_kernel().startswith("k_tile<f32,")

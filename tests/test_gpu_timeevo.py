@@ -146,3 +146,21 @@ def test_full_size_conservation():
     assert np.allclose(n2n, n2, rtol=1e-5)
     del V
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("N", [12, 20])
+def test_tiled_block_kernel_pair_swap(N):
+    """16 complex C64 columns through the tiled two-pass kernel: the pair swap
+    of the real-time step (multiplication by -i dt / j) in its second pass."""
+    bonds = random_regular_graph(N, 3, 5)
+    m, b, h = pair("SPIN_HALF_GC", N, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 8)))
+    h.set_tuning(variant=5)
+    V0 = _start(m.dim, 16, 77)
+    Vg = torch.from_numpy(V0).to(torch.complex64).cuda().contiguous()
+    Vo = Vg.cpu().numpy().astype(np.complex128).copy()
+    for step in range(3 if N <= 12 else 1):
+        n2, e, h2, n2n = hphi.hphi_time_step(h, Vg, 0.03, 6)
+        on2, oe, on2n = m.time_step(Vo, 0.03, 6)
+        assert np.allclose(n2, on2, rtol=2e-5) and np.allclose(e, oe, rtol=2e-5, atol=2e-5), step
+    assert h.ctx.last_kernel().startswith("k_tile<f32,")
+    assert np.abs(Vg.cpu().numpy() - Vo).max() < 2e-4

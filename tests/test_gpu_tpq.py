@@ -49,13 +49,17 @@ def test_tpq_sector_model():
     assert np.allclose(e, eo, rtol=1e-12) and np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)
 
 
-@pytest.mark.parametrize("coop", [-1, 0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("coop", [-1, 0, 1, 2, 3, 4, 5, "tiled"])
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_tpq_block_of_16_complex_vectors(coop, dtype):
     """16 complex vectors = 32-column rows, the fused <x,Hx>, |Hx|^2, |x|^2
-    reductions of the wide-row kernel in both bond-sharing modes."""
+    reductions of the wide-row kernel in both bond-sharing modes, and of the
+    tiled two-pass kernel (FP32 data; FP64 keeps the wide-row kernel)."""
     m, b, h = pair("SPIN_HALF_GC", 12, 0, 0, _model(12, 5))
-    h.set_tuning(variant=1, coop=coop)
+    if coop == "tiled":
+        h.set_tuning(variant=5)
+    else:
+        h.set_tuning(variant=1, coop=coop)
     V0 = random_vectors(m.dim, 16, 23, complex_=True)
     Vg = torch.from_numpy(V0).to(dtype).cuda().contiguous()
     Vo = Vg.cpu().numpy().astype(np.complex128).copy()
