@@ -200,6 +200,30 @@ def measure_dtype(ctx, ham, dim, dtype_name, K, W, dist, world):
                 vec_launches=vec_n, vec_ms=vec_ms, e0=r["e0"], steps=r["steps"], es=es)
 
 
+def issue_roofline(path, kernel_name, rows, avg_ms, sms, mhz):
+    """Issue-rate bound of the single-column kernel: warp instructions per row
+    (from a committed ncu summary of the same kernel family and source hash on
+    the 6x5 sector) x rows / (SMs x 4 schedulers x SM clock); null unless the
+    summary's kernel shares the running kernel's family and hash."""
+    if not os.path.exists(path) or "@" not in kernel_name:
+        return None
+    rec = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.split(":")[0] in ("kernel", "warp_inst_per_row"):
+                k, v = ln.split(":", 1)
+                rec[k] = v.strip()
+    if "kernel" not in rec or "warp_inst_per_row" not in rec:
+        return None
+    fam = lambda n: (n.split("<")[0] + "<" + ",".join(n.split("<")[1].split(",")[:2]), n.split("@")[-1])
+    if fam(rec["kernel"]) != fam(kernel_name):
+        return None
+    wipr = float(rec["warp_inst_per_row"])
+    bound_ms = rows * wipr / (sms * 4 * mhz * 1e6) * 1e3
+    return {"bound": "issue", "warp_inst_per_row": wipr, "bound_ms": bound_ms, "achieved_ms": avg_ms,
+            "frac": bound_ms / avg_ms, "clock_mhz": mhz, "source": "hv_single_column_square6x5_ncu.md"}
+
+
 def measure_precision(ham, dim, K):
     """Energy of the FP32-storage path against the FP64 path on the same
     workload and start vector (untimed): K Lanczos steps plus the ground-state
@@ -382,6 +406,9 @@ def run_native(args):
     # unless the summary names exactly the kernel instance that ran here
     traffic = traffic_for(os.path.join(ROOT, "profiles", f"hv_fused_square4x8_{args.dtype}_traffic.md"),
                           kernel_name)
+    mhz = (ck or {}).get("sm_mhz") or 2070.0
+    issue = issue_roofline(os.path.join(ROOT, "profiles", "hv_single_column_square6x5_ncu.md"), kernel_name, dim,
+                           hv_avg_ms, ctx.sm_count, mhz)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -403,7 +430,7 @@ def run_native(args):
                    "l2": "inputs larger than L2 (one vector = %.1f GB)" % (main["es"] * dim / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kernel_name,
-                     "peak_kind": peak_kind, "avg_launch_ms": hv_avg_ms},
+                     "peak_kind": peak_kind, "avg_launch_ms": hv_avg_ms, "issue": issue},
         "gpu_launches": gpu_launches,
         "kernel_ms": {"hv": main["hv_ms"], "vector": main["vec_ms"], "hv_launches": main["hv_launches"],
                       "vector_launches": main["vec_launches"]},
@@ -808,40 +835,47 @@ def run_szz(args):
 
 
 def run_serve(args):
-    """Serving mix: seeded Poisson arrivals (seed 5) of requests, half ground
-    states (residual 1e-10) and half S^zz(q, w) spectra (200 shifts w in
-    [0, 4] above E0, eta = 0.05, every shift's relative residual <= 1e-6,
-    q = 2 pi m / L with seeded m); models drawn from Heisenberg chains and
-    2-leg ladders with J_b ~ U[0.5, 1.5] and half-filled Hubbard 2 x L
-    clusters with U ~ U[4, 10].  Sizes are capped (N <= 22, 2 x 6) so that a
-    trace ends in about a minute; problems up to 2^17 rows run on the batched
-    block lane, larger ones on the grid lane (two workers).
-    One step = 16 requests of the trace; value = completed requests / s."""
+    """Serving mix (the fifth workload): seeded Poisson arrivals of requests,
+    half ground states (residual 1e-10) and half S^zz(q, w) spectra (200 shifts
+    w in [0, 4] above E0, eta = 0.05, every shift's relative residual <= 1e-6,
+    q = 2 pi m / L with seeded m); models drawn uniformly from Heisenberg chains
+    and 2-leg ladders with N in {18, 20, ..., 30} and J_b ~ U[0.5, 1.5], and
+    half-filled Hubbard 2 x L clusters with L in {4, 5, 6, 7} and U ~ U[4, 10].
+    Problems up to 2^17 rows run on the batched block lane (FP64), larger ones
+    on the grid lane (two workers).  The same trace is served twice, with the
+    grid lane's vectors in FP64 and in FP32 (FP64 scalars; ground-state
+    energies from the FP64 Rayleigh quotient); each time the service rate is
+    measured first (the whole trace submitted at once) and the trace then
+    arrives at 80 % of it, so p50/p99 measure service, not a growing queue.
+    The line reports the --dtype run; the other is in `other`, and the energy
+    difference of every ground state between the two is stated.
+    One step = 2 requests of the trace; value = completed requests / s."""
     import torch
     import numpy as np
     from paper_2307_13222_gb300 import hphi
     from workloads import chain, ladder, heisenberg_terms, hubbard_terms, uniform_couplings
     world, rank, local, dist, ctx = _setup(args)
     rng = np.random.default_rng(5)
-    R = 16 * args.steps
-    rate = 40.0  # requests per second
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
-    reqs, hams = [], {}
-    for i in range(R):
-        fam = rng.integers(0, 3)
-        if fam == 0:
-            N = int(rng.choice([18, 20, 22]))
-            key = ("chain", N, int(rng.integers(0, 4)))
-            terms = heisenberg_terms(chain(N), uniform_couplings(N, 0.5, 1.5, 100 + key[2]))
-            model, nu, nd, L = "SPIN_HALF", N // 2, 0, N
-        elif fam == 1:
-            N = int(rng.choice([18, 20, 22]))
-            key = ("ladder", N, int(rng.integers(0, 4)))
-            bonds = ladder(N // 2)
-            terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 200 + key[2]))
-            model, nu, nd, L = "SPIN_HALF", N // 2, 0, N // 2
+    R = 2 * args.steps
+    hams = {}
+
+    def draw(i):
+        fam = int(rng.integers(0, 3))
+        if fam < 2:
+            N = int(rng.choice(np.arange(18, 31, 2)))
+            var = int(rng.integers(0, 4))
+            if fam == 0:
+                key = ("chain", N, var)
+                terms = heisenberg_terms(chain(N), uniform_couplings(N, 0.5, 1.5, 100 + var))
+                L = N
+            else:
+                key = ("ladder", N, var)
+                bonds = ladder(N // 2)
+                terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 200 + var))
+                L = N // 2
+            model, nu, nd = "SPIN_HALF", N // 2, 0
         else:
-            Lh = int(rng.choice([4, 5, 6]))
+            Lh = int(rng.choice([4, 5, 6, 7]))
             U = float(rng.uniform(4.0, 10.0))
             key = ("hubbard", Lh, round(U, 6))
             N = 2 * Lh
@@ -852,61 +886,184 @@ def run_serve(args):
             hams[key] = (b, hphi.Hamiltonian(ctx, b, terms), L)
         kind = int(rng.integers(0, 2))
         q = 2 * np.pi * int(rng.integers(1, hams[key][2] // 2 + 1)) / hams[key][2]
-        reqs.append((arrivals[i], key, kind, int(1000 + i), q))
+        return (key, kind, int(1000 + i), q)
+
+    trace = [draw(i) for i in range(R)]
     omega = np.linspace(0.0, 4.0, 200)
-    srv = hphi.Server(ctx, 60e9, chunk=16)
-    # warm-up: the smallest request of each kind
-    w_ids = [srv.submit(hams[reqs[0][1]][1], kind=k, seed=7, max_steps=3000, tol=1e-10 if k == 0 else 1e-6,
-                        q=reqs[0][4], eta=0.05, omega=omega) for k in (0, 1)]
-    srv.run_until_done(w_ids)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    t_start = srv.clock()
-    ids, nsub, steps = [], 0, 0
-    while True:
-        now = srv.clock() - t_start
-        while nsub < R and reqs[nsub][0] <= now:
-            a, key, kind, seed, q = reqs[nsub]
-            ids.append((srv.submit(hams[key][1], kind=kind, seed=seed, max_steps=3000,
-                                   tol=1e-10 if kind == 0 else 1e-6, q=q, eta=0.05, omega=omega), a))
-            nsub += 1
-        running, queued = srv.step()
-        steps += 1
-        if nsub == R and running == 0 and queued == 0:
-            break
-        st = srv.stats()
-        if st["block_running"] == 0 and st["queued"] == 0:
-            # nothing on the block lane: wait for the next arrival or the grid lane
-            nxt = reqs[nsub][0] - (srv.clock() - t_start) if nsub < R else 0.0005
-            time.sleep(max(0.0, min(0.0005, nxt)))
-    t_end = srv.clock() - t_start
-    ck = clocks.stop()
-    res = [srv.result(i) for i, _ in ids]
-    lat = [r["t_done"] - t_start - a for r, (i, a) in zip(res, ids)]
-    ok = sum(r["status"] == 0 for r in res)
-    ms = max_over_ranks(t_end * 1e3, dist)
-    kinds = [reqs[j][2] for j in range(R)]
-    line = _base(args, world, "served_requests_per_s", world * R / (ms * 1e-3), "requests/s", ms / args.steps, "f64",
-                 {"workload": "serving_mix_poisson", "requests": R, "arrival_rate_per_s": rate,
-                  "ground_fraction": 1.0 - float(np.mean(kinds)), "shifts": 200, "eta": 0.05,
-                  "models": "chains/ladders N in {18,20,22}, Hubbard 2xL L in {4,5,6}",
-                  "form": "continuous batching: block lane (D <= 2^17, one block per recurrence) + grid lane",
-                  "parallelism": f"replicas{world}",
-                  "l2": "per-request working sets 0.4-40 MB, distinct per request (no flush)"})
-    lanes = [r["lane"] for r in res]
-    sst = srv.stats()
-    line.update({"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
-                 "completed_ok": ok, "server_steps": steps, "grid_lane_requests": int(sum(lanes)),
-                 "roofline": None,
+    MAX_STEPS = 8000
+
+    def serve(dtype):
+        srv = hphi.Server(ctx, 60e9, chunk=16, grid_dtype=dtype)
+
+        def submit(item):
+            key, kind, seed, q = item
+            return srv.submit(hams[key][1], kind=kind, seed=seed, max_steps=MAX_STEPS,
+                              tol=1e-10 if kind == 0 else 1e-6, q=q, eta=0.05, omega=omega)
+
+        def drive(arrivals):
+            t_start = srv.clock()
+            ids, nsub, busy, last = [], 0, 0.0, 0.0
+            while True:
+                now = srv.clock() - t_start
+                while nsub < R and arrivals[nsub] <= now:
+                    ids.append(submit(trace[nsub]))
+                    nsub += 1
+                running, queued = srv.step()
+                now2 = srv.clock() - t_start
+                st = srv.stats()
+                if st["block_running"] + st["grid_running"] + st["queued"] > 0:
+                    busy += now2 - last
+                last = now2
+                if nsub == R and running == 0 and queued == 0 and st["grid_running"] == 0:
+                    break
+                if st["block_running"] == 0 and st["queued"] == 0:
+                    nxt = arrivals[nsub] - now2 if nsub < R else 0.0005
+                    time.sleep(max(0.0, min(0.0005, nxt)))
+            return ids, srv.clock() - t_start, busy, t_start
+
+        small = min(trace, key=lambda it: int(hams[it[0]][1].dim))
+        srv.run_until_done([submit((small[0], k, 7, small[3])) for k in (0, 1)])  # warm-up
+        torch.cuda.synchronize()
+        _, t_cal, _, _ = drive(np.zeros(R))          # service rate: the whole trace at once
+        mu = R / t_cal
+        rate = 0.8 * mu
+        arrivals = np.cumsum(np.random.default_rng(55).exponential(1.0 / rate, R))
+        clocks = ClockSampler(local)
+        clocks.start()
+        ids, t_end, busy, t0 = drive(arrivals)
+        ck = clocks.stop()
+        res = [srv.result(i) for i in ids]
+        sst = srv.stats()
+        srv.close()
+        lat = [r["t_done"] - t0 - a for r, a in zip(res, arrivals)]
+        fails = [{"request": j, "kind": "spectrum" if trace[j][1] else "ground", "model": list(trace[j][0]),
+                  "dim": int(hams[trace[j][0]][1].dim), "status": int(r["status"]), "max_resid": r["max_resid"],
+                  "krylov_steps": r["krylov_steps"], "lanczos_steps": r["steps"]}
+                 for j, r in enumerate(res) if r["status"] != 0]
+        return {"dtype": dtype, "requests_per_s": R / t_end, "t_end": t_end, "service_rate_per_s": mu,
+                "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                "p99_ms": float(np.percentile(lat, 99)) * 1e3, "utilization": busy / t_end,
+                "completed_ok": sum(r["status"] == 0 for r in res), "failures": fails,
+                "grid_lane_requests": int(sum(r["lane"] for r in res)), "block_launches": int(sst["block_launches"]),
+                "arena_peak_gb": sst["arena_peak"] / 1e9, "clocks": ck, "e0": [r["e0"] for r in res]}
+
+    runs = {dt: serve(dt) for dt in ("f64", "f32")}
+    main, other = runs[args.dtype], runs["f32" if args.dtype == "f64" else "f64"]
+    ground = [j for j, it in enumerate(trace) if it[1] == 0]
+    errs = [abs(runs["f32"]["e0"][j] - runs["f64"]["e0"][j]) / abs(runs["f64"]["e0"][j]) for j in ground
+            if runs["f64"]["e0"][j] != 0.0]
+    ms = max_over_ranks(main["t_end"] * 1e3, dist)
+    kinds = [it[1] for it in trace]
+    line = _base(args, world, "served_requests_per_s", world * R / (ms * 1e-3), "requests/s", ms / args.steps,
+                 args.dtype, {"workload": "serving_mix_poisson", "requests": R,
+                              "arrival_rate_per_s": main["arrival_rate_per_s"],
+                              "service_rate_per_s": main["service_rate_per_s"],
+                              "ground_fraction": 1.0 - float(np.mean(kinds)), "shifts": 200, "eta": 0.05,
+                              "models": "chains/ladders N in {18..30} even, Hubbard 2xL L in {4..7}",
+                              "form": "continuous batching: block lane (D <= 2^17, FP64, one block per recurrence) + "
+                                      "grid lane (2 workers)",
+                              "grid_lane_vectors": args.dtype, "scalars": "f64",
+                              "parallelism": f"replicas{world}",
+                              "l2": "per-request working sets 0.4 MB - 7 GB, distinct per request (no flush)"})
+    line.update({"p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "utilization": main["utilization"],
+                 "offered_load": 0.8, "completed_ok": main["completed_ok"], "failures": main["failures"],
+                 "grid_lane_requests": main["grid_lane_requests"],
+                 "max_dim": int(max(h[1].dim for h in hams.values())), "roofline": None,
                  # block-lane launches counted by the server; the grid lane's drivers launch
                  # about 7 kernels per Lanczos step besides
-                 "gpu_launches": int(sst["block_launches"]), "arena_peak_gb": sst["arena_peak"] / 1e9,
+                 "gpu_launches": main["block_launches"], "arena_peak_gb": main["arena_peak_gb"],
+                 "other": {k: v for k, v in other.items() if k not in ("e0", "clocks")},
+                 "ground_e0_rel_diff_f32_vs_f64": {"max": max(errs) if errs else None,
+                                                   "median": float(np.median(errs)) if errs else None,
+                                                   "count": len(errs)},
                  "e2e": {"value": world * R / (ms * 1e-3), "unit": "requests/s", "h2d_bytes_per_step": 0,
-                         "d2h_bytes_per_step": 16 * 200 * 16}})
+                         "d2h_bytes_per_step": 200 * 16}})
+    if main["clocks"]:
+        line["clocks"] = main["clocks"]
+    return _finish(line, rank, dist, ctx)
+
+
+_FMA_SRC = r"""
+#include <torch/extension.h>
+#include <cuda_runtime.h>
+template <typename T>
+__global__ void fma_chain(T *out, int iters, T a, T b) {
+    T x[8];
+    #pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; i++) {
+        #pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+    #pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    if (s == (T)12345.678) out[0] = s;  // keeps the chain live
+}
+double run(int64_t blocks, int64_t threads, int64_t iters, bool dbl) {
+    void *out = nullptr;
+    cudaMalloc(&out, 16);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; rep++) {
+        cudaEventRecord(e0);
+        if (dbl) fma_chain<double><<<blocks, threads>>>((double *)out, (int)iters, 0.999999, 1e-7);
+        else fma_chain<float><<<blocks, threads>>>((float *)out, (int)iters, 0.999999f, 1e-7f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaFree(out);
+    return (double)ms;
+}
+PYBIND11_MODULE(TORCH_EXTENSION_NAME, m) { m.def("run", &run); }
+"""
+
+
+def run_fp64peak(args):
+    """FMA throughput of the FP64 and FP32 pipes (the bound of the FP64 H*x):
+    a chain of 8 independent multiply-adds per thread over `iters` rounds,
+    SMs x 8 blocks of 256 threads, timed with CUDA events (second launch);
+    and cuBLAS DGEMM 8192^3 through torch.matmul for comparison.
+    value = FP64 FMA per second."""
+    import torch
+    from torch.utils.cpp_extension import load_inline
+    world, rank, local, dist, ctx = _setup(args)
+    mod = load_inline("hphi_fma_probe", cpp_sources="", cuda_sources=_FMA_SRC, functions=None,
+                      extra_cuda_cflags=["-O3", "-gencode", "arch=compute_103a,code=sm_103a"], verbose=False)
+    sms = ctx.sm_count
+    blocks, threads, iters = sms * 8, 256, 20000
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64 = mod.run(blocks, threads, iters, True)
+    ms32 = mod.run(blocks, threads, iters * 8, False)
+    n = 4096 * 2
+    A = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    B = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(A, B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    torch.matmul(A, B)
+    e1.record()
+    torch.cuda.synchronize()
+    msg = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    fma64 = blocks * threads * 8.0 * iters / (ms64 * 1e-3)
+    fma32 = blocks * threads * 8.0 * iters * 8 / (ms32 * 1e-3)
+    line = _base(args, world, "fp64_fma_per_s", fma64, "FMA/s", ms64, "f64",
+                 {"workload": "fma_chain_probe", "blocks": blocks, "threads": threads, "iters": iters,
+                  "parallelism": f"replicas{world}", "l2": "register-only loop"})
+    line.update({"fp64_tflops": 2 * fma64 / 1e12, "fp32_fma_per_s": fma32, "fp32_tflops": 2 * fma32 / 1e12,
+                 "fp64_over_fp32": fma64 / fma32, "dgemm_tflops": 2.0 * n ** 3 / (msg * 1e-3) / 1e12,
+                 "per_sm_per_clock_fp64_fma": None, "roofline": None, "gpu_launches": 2})
     if ck:
         line["clocks"] = ck
-    srv.close()
+        mhz = ck.get("sm_mhz")
+        if mhz:
+            line["per_sm_per_clock_fp64_fma"] = fma64 / (sms * mhz * 1e6)
     return _finish(line, rank, dist, ctx)
 
 
@@ -962,7 +1119,7 @@ def run_apply(args):
 
 
 WORKLOADS = {"chain16": run_chain16, "hubbard4x4": run_hubbard4x4, "ctpq26": run_ctpq26, "szz": run_szz,
-             "serve": run_serve, "apply": run_apply}
+             "serve": run_serve, "apply": run_apply, "fp64peak": run_fp64peak}
 
 
 def main():

@@ -414,6 +414,14 @@ typedef struct hphi_server_opts {
     int chunk;             /* Lanczos steps per server step; 0: 16 */
     int64_t small_max_dim; /* larger problems use the grid lane; 0: 2^17 */
     int grid_workers;      /* grid-lane worker threads, each with its own stream; 0: 2 */
+    int grid_dtype;        /* vector storage of the grid lane: HPHI_F64 (0, default) or
+                              HPHI_F32 (scalars, reductions and the tridiagonal
+                              problem stay FP64; the Lanczos recurrence runs to a
+                              residual of max(tol, 1e-6), as FP32 vectors hold no
+                              more; a ground-state request then also builds its
+                              ground-state vector and reports the FP64 Rayleigh
+                              quotient of it as e0, see e0_rq of
+                              hphi_lanczos_result); the block lane is FP64 */
 } hphi_server_opts;
 
 #define HPHI_REQ_GROUND 0

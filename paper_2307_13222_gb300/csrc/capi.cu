@@ -5,6 +5,10 @@
 
 #include <new>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "hphi_internal.cuh"
 
 namespace hphi {
@@ -54,6 +58,42 @@ int ensure_dscal(hphi_ctx *ctx, size_t n) {
     if (e != cudaSuccess) return cuda_err(ctx, e, "pinned scalar buffer");
     ctx->dscal_n = n;
     return HPHI_OK;
+}
+
+int dyn_occupancy(hphi_ctx *ctx, const void *fn, int threads, size_t dyn) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> limit;              // raised limit per (kernel, device)
+    static std::map<std::tuple<const void *, int, size_t>, int> occupancy;  // per (kernel, device, size)
+    std::lock_guard<std::mutex> lk(mu);
+    const int dev = ctx->device;
+    auto key = std::make_pair(fn, dev);
+    auto it = limit.find(key);
+    if (it == limit.end()) {
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const size_t mx = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        it = limit.emplace(key, mx).first;
+    }
+    if (dyn > it->second) return 0;
+    auto ok = std::make_tuple(fn, dev, dyn);
+    auto jt = occupancy.find(ok);
+    if (jt != occupancy.end()) return jt->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    occupancy.emplace(ok, n);
+    return n;
 }
 
 int ensure_vecs(hphi_ctx *ctx, size_t bytes) {

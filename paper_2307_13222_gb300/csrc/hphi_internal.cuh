@@ -235,6 +235,15 @@ int ensure_partials(hphi_ctx *ctx, size_t n);
 int ensure_dscal(hphi_ctx *ctx, size_t n);
 int ensure_vecs(hphi_ctx *ctx, size_t bytes);
 
+// ---- dynamic shared memory (capi.cu) -------------------------------------------
+// Occupancy (thread blocks per SM) of kernel fn with `threads` threads and
+// `dyn` bytes of dynamic shared memory on the context's device.  The first
+// call for a (kernel, device) raises the kernel's dynamic shared-memory limit
+// to everything the device allows next to its static shared memory, so the
+// limit never goes down and launches of one kernel with different sizes from
+// several host threads cannot undercut one another.  Thread-safe.
+int dyn_occupancy(hphi_ctx *ctx, const void *fn, int threads, size_t dyn);
+
 // ---- kernel timing (capi.cu): returns a slot, -1 when not profiling ----------
 int prof_begin(hphi_ctx *ctx, int kind);
 void prof_end(hphi_ctx *ctx, int slot);

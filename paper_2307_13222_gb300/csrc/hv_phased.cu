@@ -275,18 +275,9 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
 template <typename T, int NT, int RED, int MINB>
 int go_p(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len, int *grid_out) {
     const size_t dyn = ((2 * (size_t)xs_len * sizeof(T) + 15) & ~(size_t)15) + 3 * (NT / 32) * sizeof(double);
-    static int occ[64] = {0};
-    static size_t occ_dyn[64] = {0};
-    const int dev = ctx->device;
-    if (occ[dev] == 0 || occ_dyn[dev] != dyn) {
-        cudaFuncSetAttribute(k_hvp<T, NT, RED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvp<T, NT, RED, MINB>, NT, dyn);
-        occ[dev] = n;
-        occ_dyn[dev] = dyn;
-    }
-    if (occ[dev] < 1) return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: a row block does not fit in shared memory");
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count;
+    const int occ = dyn_occupancy(ctx, (const void *)k_hvp<T, NT, RED, MINB>, NT, dyn);
+    if (occ < 1) return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: a row block does not fit in shared memory");
+    int64_t g = (int64_t)occ * ctx->sm_count;
     if (g > ham->nh) g = ham->nh;
     if (g < 1) g = 1;
     *grid_out = (int)g;

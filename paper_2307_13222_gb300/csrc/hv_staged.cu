@@ -201,18 +201,9 @@ __global__ void __launch_bounds__(kStagedThreads, MINB) k_hvs(const HvArgs<T> a,
 template <typename T, int RED, int TAB, int MINB>
 int go_s(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, uint32_t xs_len, int *grid_out) {
     const size_t dyn = ((xs_len * sizeof(T) + 15) & ~(size_t)15) + 3 * (kStagedThreads / 32) * sizeof(double);
-    static int occ[64] = {0};
-    static size_t occ_dyn[64] = {0};
-    const int dev = ctx->device;
-    if (occ[dev] == 0 || occ_dyn[dev] != dyn) {
-        cudaFuncSetAttribute(k_hvs<T, RED, TAB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvs<T, RED, TAB, MINB>, kStagedThreads, dyn);
-        occ[dev] = n;
-        occ_dyn[dev] = dyn;
-    }
-    if (occ[dev] < 1) return set_err(ctx, HPHI_E_INVAL, "staged H*x: a row block does not fit in shared memory");
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count;
+    const int occ = dyn_occupancy(ctx, (const void *)k_hvs<T, RED, TAB, MINB>, kStagedThreads, dyn);
+    if (occ < 1) return set_err(ctx, HPHI_E_INVAL, "staged H*x: a row block does not fit in shared memory");
+    int64_t g = (int64_t)occ * ctx->sm_count;
     if (g > ham->nh) g = ham->nh;
     if (g < 1) g = 1;
     *grid_out = (int)g;

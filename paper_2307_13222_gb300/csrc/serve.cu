@@ -342,25 +342,34 @@ void grid_worker(hphi_server *S) {
         double e0 = 0.0, mres = 0.0;
         int steps = 0, ksteps = 0;
         std::vector<double> dz;
-        double *v = nullptr, *gs = nullptr, *ex = nullptr;
-        if (!status && cudaMalloc(&v, 8 * (size_t)D) != cudaSuccess) status = HPHI_E_NOMEM;
+        // vector storage: FP64, or FP32 with FP64 scalars (then a ground state
+        // also takes the ground-state vector, whose FP64 Rayleigh quotient is the
+        // reported energy)
+        const int vdt = S->opts.grid_dtype == HPHI_F32 ? HPHI_F32 : HPHI_F64;
+        const size_t es = vdt == HPHI_F32 ? 4 : 8;
+        void *v = nullptr, *gs = nullptr, *ex = nullptr;
+        if (!status && cudaMalloc(&v, es * (size_t)D) != cudaSuccess) status = HPHI_E_NOMEM;
         const bool spec = q->r.kind == HPHI_REQ_SPECTRUM;
-        if (!status && spec && (cudaMalloc(&gs, 8 * (size_t)D) != cudaSuccess ||
-                                cudaMalloc(&ex, 16 * (size_t)D) != cudaSuccess))
-            status = HPHI_E_NOMEM;
-        if (!status) status = hphi_random_vector(gc, HPHI_F64, D, 1, q->r.seed, v, 1);
+        const bool want_gs = spec || vdt == HPHI_F32;
+        if (!status && want_gs && cudaMalloc(&gs, es * (size_t)D) != cudaSuccess) status = HPHI_E_NOMEM;
+        if (!status && spec && cudaMalloc(&ex, 2 * es * (size_t)D) != cudaSuccess) status = HPHI_E_NOMEM;
+        if (!status) status = hphi_random_vector(gc, vdt, D, 1, q->r.seed, v, 1);
         if (!status) {
-            hphi_lanczos_opts o{q->r.max_steps, q->r.tol, HPHI_F64, 1, 0};
+            // FP32 storage holds the vectors to about 1e-6 relative: the recurrence
+            // stops there and the energy comes from the FP64 Rayleigh quotient,
+            // whose error is quadratic in the vector's
+            const double ltol = (vdt == HPHI_F32 && q->r.tol > 0.0 && q->r.tol < 1e-6) ? 1e-6 : q->r.tol;
+            hphi_lanczos_opts o{q->r.max_steps, ltol, vdt, 1, 0};
             hphi_lanczos_result res{};
-            status = hphi_lanczos(gc, h, &o, v, spec ? gs : nullptr, nullptr, nullptr, &res);
-            e0 = res.e0;
+            status = hphi_lanczos(gc, h, &o, v, want_gs ? gs : nullptr, nullptr, nullptr, &res);
+            e0 = (vdt == HPHI_F32 && !spec && res.e0_rq == res.e0_rq) ? res.e0_rq : res.e0;
             steps = res.steps;
         }
         if (!status && spec) {
             std::vector<double> w;
             bool im = false;
             weights_of(q, w, &im);
-            status = hphi_apply_sz_sum(gc, h->basis, HPHI_F64, gs, 1, ex, 2, w.data());
+            status = hphi_apply_sz_sum(gc, h->basis, vdt, gs, 1, ex, 2, w.data());
             if (!status) {
                 const int nz = (int)q->omega.size();
                 std::vector<double> z(2 * (size_t)nz), g(4 * (size_t)nz), rr(2 * (size_t)nz);
@@ -368,7 +377,7 @@ void grid_worker(hphi_server *S) {
                     z[2 * j] = e0 + q->omega[j];
                     z[2 * j + 1] = q->r.eta;
                 }
-                hphi_krylov_opts ko{q->r.max_steps, q->r.tol, HPHI_F64, 4};
+                hphi_krylov_opts ko{q->r.max_steps, q->r.tol, vdt, 4};
                 hphi_krylov_result kr{};
                 status = hphi_shifted_krylov(gc, (hphi_ham *)h, &ko, im ? 2 : 1, ex, 2, nz, z.data(), g.data(),
                                              rr.data(), nullptr, nullptr, &kr);
@@ -408,7 +417,8 @@ extern "C" int hphi_server_create(hphi_ctx *ctx, const hphi_server_opts *opts, h
     ctx->err.clear();
     *out = nullptr;
     if (!(opts->mem_budget > 0) || opts->max_active < 0 || opts->chunk < 0 || opts->small_max_dim < 0 ||
-        opts->grid_workers < 0 || opts->grid_workers > 16)
+        opts->grid_workers < 0 || opts->grid_workers > 16 ||
+        (opts->grid_dtype != HPHI_F64 && opts->grid_dtype != HPHI_F32))
         return set_err(ctx, HPHI_E_INVAL, "server options");
     HPHI_CUDA(ctx, cudaSetDevice(ctx->device));
     std::unique_ptr<hphi_server> S(new (std::nothrow) hphi_server());

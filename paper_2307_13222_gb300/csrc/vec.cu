@@ -611,7 +611,8 @@ int launch_mdot(hphi_ctx *ctx, int real_dtype, int64_t n, int nv, const void *V,
     if (g < 1) g = 1;
     if ((st = ensure_partials(ctx, (size_t)g * nv))) return st;
     const size_t dyn = sizeof(double) * (kMT / 32) * nv;
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_mdot_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (dyn > 48 * 1024 && dyn_occupancy(ctx, (const void *)k_mdot_tiled<float>, kMT, dyn) < 1)
+        return set_err(ctx, HPHI_E_INVAL, "multi-vector dot: %d vectors need too much shared memory", nv);
     const int slot = prof_begin(ctx, PROF_VEC);
     k_mdot_tiled<float><<<(unsigned)g, kMT, dyn, ctx->stream>>>(n, nv, (const float *)V, (const float *)w,
                                                                ctx->partials);

@@ -54,7 +54,7 @@ class _KrylovResult(C.Structure):
 
 class _ServerOpts(C.Structure):
     _fields_ = [("mem_budget", C.c_double), ("max_active", C.c_int), ("chunk", C.c_int),
-                ("small_max_dim", C.c_int64), ("grid_workers", C.c_int)]
+                ("small_max_dim", C.c_int64), ("grid_workers", C.c_int), ("grid_dtype", C.c_int)]
 
 
 class _Request(C.Structure):
@@ -490,9 +490,12 @@ class Server:
     GROUND, SPECTRUM = 0, 1
 
     def __init__(self, ctx: Context, mem_budget: float, max_active: int = 0, chunk: int = 0, small_max_dim: int = 0,
-                 grid_workers: int = 0):
+                 grid_workers: int = 0, grid_dtype: str = "f64"):
         self.ctx = ctx
-        o = _ServerOpts(float(mem_budget), max_active, chunk, small_max_dim, grid_workers)
+        if grid_dtype not in ("f64", "f32"):
+            raise ValueError("grid_dtype is 'f64' or 'f32'")
+        o = _ServerOpts(float(mem_budget), max_active, chunk, small_max_dim, grid_workers,
+                        F32 if grid_dtype == "f32" else F64)
         h = vp()
         ctx._sync_stream()
         ctx.check(ctx.lib.hphi_server_create(ctx.h, C.byref(o), C.byref(h)))

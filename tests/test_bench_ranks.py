@@ -81,3 +81,14 @@ def test_source_tag_tracks_the_kernel_sources():
     assert len(t) == 10 and all(c in "0123456789abcdef" for c in t)
     assert "hv_phased.cu" in build.HV_SOURCES and all(f in build.SOURCES or f.endswith(".cuh")
                                                       for f in build.HV_SOURCES)
+
+
+def test_issue_roofline_matches_family_and_hash(tmp_path):
+    import bench
+    f = tmp_path / "p.md"
+    f.write_text("text\nkernel: k_hvp<f32,512,RED0,MINB2>@0123456789\nwarp_inst_per_row: 29.0\n")
+    r = bench.issue_roofline(str(f), "k_hvp<f32,512,RED1,MINB2>@0123456789", 1000000, 2.0, 100, 2000)
+    # 1e6 rows x 29 / (100 SMs x 4 x 2e9 per s) = 0.03625 ms
+    assert r is not None and abs(r["bound_ms"] - 0.03625) < 1e-12 and abs(r["frac"] - 0.018125) < 1e-12
+    assert bench.issue_roofline(str(f), "k_hvp<f32,512,RED1,MINB2>@9876543210", 10, 1.0, 1, 1) is None
+    assert bench.issue_roofline(str(f), "k_hvp<f64,1024,RED1,MINB1>@0123456789", 10, 1.0, 1, 1) is None

@@ -102,3 +102,29 @@ def test_grid_lane_agrees_with_block_lane():
     assert a["lane"] == 0 and b["lane"] == 1 and b["status"] == 0
     assert abs(a["e0"] - b["e0"]) < 1e-11 * abs(a["e0"])
     assert np.abs(a["D"] - b["D"]).max() < 1e-7 * np.abs(a["D"]).max()
+
+
+def test_grid_lane_fp32_storage_error_stated():
+    """The grid lane with FP32 vectors (FP64 scalars): a ground state's energy
+    is the FP64 Rayleigh quotient of its FP32 ground-state vector, within 1e-9
+    of the dense ground energy; a spectrum's D(z) within FP32 accuracy of the
+    dense resolvent."""
+    terms = heisenberg_terms(chain(14), uniform_couplings(14, 0.5, 1.5, 3))
+    m, b, h = pair("SPIN_HALF", 14, 7, 0, terms)
+    H = O.dense_matrix(m)
+    E, U = np.linalg.eigh(H)
+    srv = hphi.Server(ctx(), 2e9, small_max_dim=16, grid_dtype="f32")
+    ids = [srv.submit(h, kind=0, seed=11, max_steps=600, tol=1e-8),
+           srv.submit(h, kind=1, seed=12, max_steps=600, tol=1e-5, q=2 * np.pi / 14, eta=ETA, omega=OMEGA)]
+    srv.run_until_done(ids)
+    g, s = srv.result(ids[0]), srv.result(ids[1])
+    srv.close()
+    assert g["status"] == 0 and g["lane"] == 1
+    err = abs(g["e0"] - E[0]) / abs(E[0])
+    assert err < 1e-9, err
+    assert s["status"] == 0 and s["lane"] == 1
+    phi = m.sz_sum(U[:, 0], np.exp(1j * (2 * np.pi / 14) * np.arange(14)))
+    want = S.resolvent_dense(H, phi, s["e0"] + OMEGA + 1j * ETA)
+    assert np.abs(s["D"] - want).max() < 2e-3 * np.abs(want).max()
+    with pytest.raises(ValueError):
+        hphi.Server(ctx(), 2e9, grid_dtype="f16")
