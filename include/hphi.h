@@ -174,12 +174,14 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         N_lo <= 16), 3 = bond-major: the staged block's H x
  *                         accumulated in shared memory one bond at a time over
  *                         precomputed lists of the rows the bond applies to
- *                         (same shapes as 2), 4 = segment: two passes, the
- *                         high-high and the low-part/high bonds strip by
- *                         strip of the low half's upper bits (each strip
- *                         L2-resident), the rest block by block with the
- *                         targets ranked from shared tables (same shapes as
- *                         2, at most 32 bonds of each class, D < 2^31)
+ *                         (same shapes as 2), 4 = a streaming pass for the
+ *                         high-high bonds over L2-sized chunks of the low
+ *                         half, then the bond-major kernel without them
+ *                         (same shapes as 3, D < 2^31; on request), 5 =
+ *                         tiled: full space, 32 FP32 columns, the bonds split
+ *                         over two passes that each gather only inside an
+ *                         L2-resident tile of rows (automatic there when the
+ *                         bond graph has such a split)
  *   HPHI_TUNE_COOP        32-column rows: 1-5 = the lanes of a row split the
  *                         bond evaluation and share targets (1: 8 targets per
  *                         batch, registers for 2 thread blocks per SM; 2: 4

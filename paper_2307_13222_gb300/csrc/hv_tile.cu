@@ -39,6 +39,8 @@ namespace {
 
 constexpr int kTileThreads = 256;
 constexpr int kTileItemBits = 5;  // 32 rows (4 per warp) per thread-block iteration
+constexpr int kTileUnroll = 8;    // bonds tested and gathered per batch (4: 7 % slower)
+constexpr int kTileMinB1 = 4;     // thread blocks per SM the registers of pass 1 are sized for
 
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
     asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
@@ -68,9 +70,9 @@ __global__ void k_tile_diag(const DTerm *terms, int nt, int64_t D, float *d) {
 
 // One pass.  PASS 1 writes t; PASS 2 reads t and applies the epilogue.
 // Eight lanes per row, four columns (16 bytes) each; four rows per warp;
-// four bonds (tested, their targets loaded) in flight.
+// kTileUnroll bonds (tested, their targets loaded) in flight.
 template <int PASS, int RED>
-__global__ void __launch_bounds__(kTileThreads, (PASS == 1 || RED == 0) ? 4 : 3)
+__global__ void __launch_bounds__(kTileThreads, PASS == 1 ? kTileMinB1 : (RED == 0 ? 4 : 3))
     k_tile(const HvArgs<float> a, const TileArgs ta, const float *__restrict__ diag, float *tbuf) {
     __shared__ uint32_t pin[4][256], pout[4][256];
     __shared__ uint32_t bm[kTileMaxBonds];
@@ -120,17 +122,17 @@ __global__ void __launch_bounds__(kTileThreads, (PASS == 1 || RED == 0) ? 4 : 3)
             ldc4(tbuf + roff, acc);
         }
         int k = 0;
-        for (; k + 4 <= nb; k += 4) {
-            float v[4][4];
-            bool ok[4];
+        for (; k + kTileUnroll <= nb; k += kTileUnroll) {
+            float v[kTileUnroll][4];
+            bool ok[kTileUnroll];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
+            for (int u = 0; u < kTileUnroll; u++) {
                 const uint32_t m = bm[k + u];
                 ok[u] = __popc(s & m) == 1;
                 if (ok[u]) ld4(X + (uint64_t)(s ^ m) * 32 + 4 * gl, v[u]);
             }
 #pragma unroll
-            for (int u = 0; u < 4; u++)
+            for (int u = 0; u < kTileUnroll; u++)
                 if (ok[u]) {
                     const float c = bc[k + u];
 #pragma unroll
