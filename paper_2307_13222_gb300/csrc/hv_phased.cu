@@ -38,6 +38,24 @@ template <typename T> constexpr int kPhUnrollLL = sizeof(T) == 4 ? 8 : 4;
 constexpr int kPhGathers = 4;  // high-high gathers in flight per row
 constexpr int kPhMaxLL = 128;
 
+// U list entries of one low-low bond per lane (entry i = first + 32 u): acs[q] += c xs[q'].
+template <typename T, int U, bool PRED>
+__device__ __forceinline__ void ll_batch(const uint32_t *__restrict__ ent, int32_t first, int32_t end, T c,
+                                         const T *xs, T *acs) {
+    uint32_t pk[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int32_t i = first + 32 * u;
+        pk[u] = (!PRED || i < end) ? __ldg(ent + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (!PRED || first + 32 * u < end) {
+            const uint32_t q = pk[u] & 0xFFFFu;
+            acs[q] = fma(c, xs[pk[u] >> 16], acs[q]);
+        }
+}
+
 template <typename T, int NT, int RED, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs_len) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -139,20 +157,21 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
                 const int32_t s0 = __shfl_sync(0xffffffffu, my0, j), s1 = __shfl_sync(0xffffffffu, my1, j);
                 if (s0 == s1) continue;
                 const T ck = ll_c[k0 + j];
-                for (int32_t i0 = s0 + lane; i0 < s1; i0 += 32 * kPhUnrollLL<T>) {
-                    uint32_t pk[kPhUnrollLL<T>];
-#pragma unroll
-                    for (int u = 0; u < kPhUnrollLL<T>; u++) {
-                        const int32_t i = i0 + 32 * u;
-                        pk[u] = i < s1 ? __ldg(ent + i) : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kPhUnrollLL<T>; u++)
-                        if (i0 + 32 * u < s1) {
-                            const uint32_t q = pk[u] & 0xFFFFu;
-                            acs[q] = fma(ck, xs[pk[u] >> 16], acs[q]);
-                        }
+                // full batches of kPhUnrollLL entries per lane, then halving batches,
+                // then one predicated batch of two: no lane slot idles in a batch but
+                // the last (a row occurs once per bond, so batches need no ordering)
+                int32_t b = s0;
+                for (; b + 32 * kPhUnrollLL<T> <= s1; b += 32 * kPhUnrollLL<T>)
+                    ll_batch<T, kPhUnrollLL<T>, false>(ent, b + lane, s1, ck, xs, acs);
+                if (kPhUnrollLL<T> > 4 && b + 128 <= s1) {
+                    ll_batch<T, 4, false>(ent, b + lane, s1, ck, xs, acs);
+                    b += 128;
                 }
+                if (b + 64 <= s1) {
+                    ll_batch<T, 2, false>(ent, b + lane, s1, ck, xs, acs);
+                    b += 64;
+                }
+                if (b < s1) ll_batch<T, 2, true>(ent, b + lane, s1, ck, xs, acs);
                 __syncwarp();
             }
         }
