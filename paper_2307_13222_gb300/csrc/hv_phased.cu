@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hvp(const HvArgs<T> a, uint32_t xs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T *__restrict__ dlow = (const T *)P.dlow;
     const T *__restrict__ X = a.x;
-    const uint32_t ld = (uint32_t)a.ldx;
+    constexpr uint32_t ld = 1;  // x, y and v are contiguous vectors (the launcher checks)
     const uint32_t *__restrict__ ent = P.ph_ent;
     constexpr int OS = kPhRanges + 1;  // offsets per list group
     // reductions: each warp folds its rows of a block into its slots of red_sm
@@ -318,6 +318,8 @@ int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int re
     const int nlists = ham->model == HPHI_HUBBARD ? ham->host.n_ncoef : ham->host.n_ll;
     if (!a.P.ph_ent || nlists > kPhMaxLL)
         return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: no bond lists for this Hamiltonian");
+    if (a.ldx != 1 || a.ldy != 1 || (a.v && a.ldv != 1))
+        return set_err(ctx, HPHI_E_INVAL, "bond-major H*x: one contiguous column only");
     const uint32_t xl = staged_block_len(ham);
     constexpr bool F = std::is_same<T, float>::value;
     constexpr int NT = F ? 512 : 1024, MB = F ? 2 : 1;
