@@ -40,17 +40,22 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-# sources that decide the code and tables of the H*x kernels
-HV_SOURCES = ["basis.cu", "ham.cu", "hv.cu", "hv_lean.cu", "hv_fly.cu", "hv_staged.cu", "hv_phased.cu", "hv_seg.cu", "hv_tile.cu",
-              "hvcommon.cuh", "rowvisit.cuh", "hphi_internal.cuh"]
+# sources every H*x kernel's code and tables depend on: the shared headers and
+# the basis / Hamiltonian table builders
+HV_COMMON = ["basis.cu", "ham.cu", "hvcommon.cuh", "rowvisit.cuh", "hphi_internal.cuh"]
+# units that name kernels defined in other files (hv.cu launches the lean and
+# the on-the-fly kernels)
+TAG_DEPS = {"hv.cu": ["hv_lean.cu", "hv_fly.cu"]}
 
 
-def source_tag() -> str:
-    """Short hash of the H*x kernel sources: hphi_last_kernel appends it to the
-    kernel name, so a profile taken on other kernel sources does not match."""
+def source_tag(unit: str = "hv.cu") -> str:
+    """Short hash of one translation unit and the sources its H*x kernels
+    depend on: hphi_last_kernel appends it to the kernel name, so a profile
+    taken on other sources of that kernel does not match (and one taken
+    before a change to another kernel's file still does)."""
     import hashlib
     h = hashlib.sha1()
-    for f in HV_SOURCES:
+    for f in [unit] + TAG_DEPS.get(unit, []) + HV_COMMON:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:10]
@@ -61,10 +66,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(OUT, exist_ok=True)
-    inc = ["-I", os.path.join(ROOT, "include"), f"-DHPHI_SRC_TAG=\"{source_tag()}\""]
-
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        inc = ["-I", os.path.join(ROOT, "include"), f"-DHPHI_SRC_TAG=\"{source_tag(src)}\""]
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + ARCH + FLAGS + inc
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

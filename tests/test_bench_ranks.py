@@ -75,12 +75,14 @@ def test_traffic_is_reported_only_for_the_captured_kernel(tmp_path):
 
 
 def test_source_tag_tracks_the_kernel_sources():
+    """One tag per translation unit: its own source and the shared headers and
+    table builders; kernels in different files get different tags."""
     import importlib
     build = importlib.import_module("paper_2307_13222_gb300.build")
-    t = build.source_tag()
+    t = build.source_tag("hv_phased.cu")
     assert len(t) == 10 and all(c in "0123456789abcdef" for c in t)
-    assert "hv_phased.cu" in build.HV_SOURCES and all(f in build.SOURCES or f.endswith(".cuh")
-                                                      for f in build.HV_SOURCES)
+    assert t != build.source_tag("hv_tile.cu") and t == build.source_tag("hv_phased.cu")
+    assert all(f in build.SOURCES or f.endswith(".cuh") for f in build.HV_COMMON)
 
 
 def test_issue_roofline_matches_family_and_hash(tmp_path):
