@@ -278,27 +278,62 @@ def measure_block_leg(ctx, steps=2, autotune=True):
     avg = ms / max(n, 1)
     peak, kind = peaks()
     ach = stage_bytes / (avg * 1e-3) / 1e9
+    # DRAM bytes per stage from the committed ncu summary of the same kernel
+    # pair and sources (the stages differ only in their reductions)
+    traffic = traffic_for(os.path.join(ROOT, "profiles", "hv_tiled_block_rrg26_c64_traffic.md"), kernel,
+                          key="bytes_per_stage", same_family=True)
     return {"workload": "ctpq_rrg3_N26_B16_c64", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_kind": "of measured" if kind == "measured" else "of fallback",
-            "avg_stage_ms": avg, "stages": n, "bytes_per_stage": stage_bytes, "kernel": kernel,
+            "traffic": traffic, "avg_stage_ms": avg, "stages": n, "bytes_per_stage": stage_bytes, "kernel": kernel,
             "autotuned_ms": tuned[0] if tuned else None}
 
 
-def traffic_for(path, kernel_name):
+def traffic_for(path, kernel_name, key="bytes_per_launch", same_family=False):
     """DRAM bytes per launch from a committed ncu summary, or None unless the
     summary's `kernel:` line names exactly the kernel instance that ran (its
-    template arguments and the hash of the H*x sources it was built from)."""
-    if not os.path.exists(path):
+    template arguments and the hash of the sources it was built from); with
+    same_family, the kernel name before its template arguments and the hash
+    must agree."""
+    if not os.path.exists(path) or not kernel_name:
         return None
     rec = {}
     with open(path) as f:
         for ln in f:
-            if ":" in ln and ln.split(":")[0] in ("kernel", "bytes_per_launch"):
+            if ":" in ln and ln.split(":")[0] in ("kernel", key):
                 k, v = ln.split(":", 1)
-                rec[k] = v.strip()
-    if rec.get("kernel") == kernel_name and "bytes_per_launch" in rec:
-        return float(rec["bytes_per_launch"])
-    return None
+                rec.setdefault(k, v.strip())
+    if key not in rec or "kernel" not in rec:
+        return None
+    if same_family:
+        fam = lambda n: (n.split("<")[0], n.split("@")[-1] if "@" in n else None)
+        ok = "@" in rec["kernel"] and fam(rec["kernel"]) == fam(kernel_name)
+    else:
+        ok = rec["kernel"] == kernel_name
+    return float(rec[key]) if ok else None
+
+
+def gpu_local_cpus(dev):
+    """The host CPUs next to GPU `dev` (its PCI device's local_cpulist), or None."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        dom, bus, d = p.pci_domain_id, p.pci_bus_id, p.pci_device_id
+        with open(f"/sys/bus/pci/devices/{dom:04x}:{bus:02x}:{d:02x}.0/local_cpulist") as f:
+            txt = f.read().strip()
+    except Exception:  # no PCI ids in this torch, no sysfs entry, no GPU
+        return None
+    return parse_cpulist(txt)
+
+
+def parse_cpulist(txt):
+    """CPU set of a sysfs cpulist ("0-71,144-215"), or None when empty."""
+    cpus = set()
+    for part in txt.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus or None
 
 
 def measure_e2e(ctx, ham, dim, dtype_name, K, world=1):
@@ -322,8 +357,24 @@ def measure_e2e(ctx, ham, dim, dtype_name, K, world=1):
         return dict(skipped=f"one host vector pair ({2 * es * dim} bytes) exceeds a quarter of the node's memory "
                             f"shared among {world} ranks")
     nb = min(max(K, 1), 8, fit)
-    xh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
-    yh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
+    # pinned buffers on the GPU's own host memory node: allocated (and first
+    # touched) from the CPUs next to the GPU; a remote node's memory halves or
+    # worse the device's reads over the host link
+    local = gpu_local_cpus(torch.cuda.current_device())
+    saved = os.sched_getaffinity(0) if local else None
+    if local:
+        try:
+            os.sched_setaffinity(0, local & saved or local)
+        except OSError:
+            local = None
+    try:
+        xh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
+        yh = torch.empty((nb, dim), dtype=tdt, pin_memory=True)
+        xh.zero_()
+        yh.zero_()
+    finally:
+        if saved:
+            os.sched_setaffinity(0, saved)
     xd = torch.empty(dim, dtype=tdt, device="cuda")
     for k in range(nb):
         hphi.hphi_random_vector(ctx, xd, 3 + k)
@@ -351,6 +402,7 @@ def measure_e2e(ctx, ham, dim, dtype_name, K, world=1):
         link[name] = es * dim / (time.perf_counter() - t0) / 1e9
     del xh, yh, xd
     torch.cuda.empty_cache()
+    link["buffers_on"] = f"GPU-local CPUs ({len(local)})" if local else "default placement"
     return dict(value=2.0 * es * dim / (ms * 1e-3) / 1e9, ms=ms, h2d=es * dim, d2h=es * dim, batch=nb, calls=calls,
                 link=link)
 
@@ -666,7 +718,16 @@ def run_hubbard4x4(args):
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
         es = 4 if tdt == torch.float32 else 8
-        out[dt_name] = dict(ms=ms, r=r, roof=_roofline(ctx, 3.0 * es * b.dim, ctx.last_kernel()))
+        roof = _roofline(ctx, 3.0 * es * b.dim, None)
+        ctx.profile(False)
+        # the name of the steps' H*x kernel (the last launch inside the solve is the
+        # FP64 H*x of the Rayleigh quotient, counted in `launches` above): one
+        # untimed product of the same precision
+        hphi.hphi_apply_H(h, v0, gs)
+        torch.cuda.synchronize()
+        roof["kernel"] = ctx.last_kernel()
+        roof["launches_note"] = "the Lanczos steps' H*x plus one FP64 H*x of the Rayleigh quotient"
+        out[dt_name] = dict(ms=ms, r=r, roof=roof)
         del v0, gs
         torch.cuda.empty_cache()
     ck = clocks.stop()

@@ -94,3 +94,18 @@ def test_issue_roofline_matches_family_and_hash(tmp_path):
     assert r is not None and abs(r["bound_ms"] - 0.03625) < 1e-12 and abs(r["frac"] - 0.018125) < 1e-12
     assert bench.issue_roofline(str(f), "k_hvp<f32,512,RED1,MINB2>@9876543210", 10, 1.0, 1, 1) is None
     assert bench.issue_roofline(str(f), "k_hvp<f64,1024,RED1,MINB1>@0123456789", 10, 1.0, 1, 1) is None
+
+
+def test_parse_cpulist():
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("") is None
+
+
+def test_traffic_for_same_family(tmp_path):
+    import bench
+    f = tmp_path / "t.md"
+    f.write_text("kernel: k_tile<f32,RED0>x2@0123456789\nbytes_per_stage: 77\n")
+    assert bench.traffic_for(str(f), "k_tile<f32,RED3>x2@0123456789", key="bytes_per_stage", same_family=True) == 77.0
+    assert bench.traffic_for(str(f), "k_tile<f32,RED3>x2@9999999999", key="bytes_per_stage", same_family=True) is None
+    assert bench.traffic_for(str(f), "k_tile<f32,RED3>x2@0123456789", key="bytes_per_stage") is None
