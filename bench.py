@@ -242,7 +242,8 @@ def measure_precision(ham, dim, K):
         del v0, gs
         torch.cuda.empty_cache()
     ref = out["f64"][1]
-    return {"steps": K, "e0_f64_rq": ref, "ritz_rel_err_f32": abs(out["f32"][0] - ref) / abs(ref),
+    return {"steps": K, "e0_f64_rq": ref, "e0_f64_ritz": out["f64"][0], "e0_f32_ritz": out["f32"][0],
+            "ritz_rel_err_f32": abs(out["f32"][0] - ref) / abs(ref),
             "rq_rel_err_f32": abs(out["f32"][1] - ref) / abs(ref), "ritz_rel_err_f64": abs(out["f64"][0] - ref) / abs(ref)}
 
 
@@ -447,6 +448,12 @@ def run_native(args):
     if args.dtype == "f32" and not args.no_fp64:
         other = measure_dtype(ctx, ham, dim, "f64", max(2, K // 4), 1, dist, world)
     prec = measure_precision(ham, dim, K) if args.dtype == "f32" and not args.no_fp64 else None
+    # the oracle's 20-step FP64 run from the same start vector (when the golden is present)
+    gold20 = None
+    gpath = os.path.join(ROOT, "tests", "golden", "lanczos_square4x8_20steps.json")
+    if os.path.exists(gpath) and K == 20:
+        with open(gpath) as fh:
+            gold20 = json.load(fh)["e0"]
     block = measure_block_leg(ctx, autotune=not args.no_autotune) if not args.no_block else None
     peak, peak_kind = peaks()
     # dominant kernel: the fused H*x of the Lanczos step; algorithmic bytes per
@@ -504,6 +511,11 @@ def run_native(args):
     if cpu:
         line["cpu_baseline"] = cpu
     if prec:
+        if gold20 is not None:
+            # the Ritz values after the same 20 steps against the oracle's FP64 run
+            prec["e0_oracle_golden_20_steps"] = gold20
+            prec["ritz_rel_err_vs_oracle"] = {"f32": abs(prec["e0_f32_ritz"] - gold20) / abs(gold20),
+                                              "f64": abs(prec["e0_f64_ritz"] - gold20) / abs(gold20)}
         line["precision"] = prec
     if block:
         line["block"] = block

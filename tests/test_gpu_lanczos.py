@@ -178,3 +178,35 @@ def test_hubbard4x4_energy_against_the_oracle_golden():
     print(f"4x4 Hubbard FP32 storage: Ritz value error {err_ritz:.2e}, FP64 Rayleigh quotient error {err_rq:.2e}")
     assert err_ritz < 1e-6
     assert err_rq <= 1e-8, (err_rq, err_ritz)
+
+
+def test_square4x8_lanczos_20_steps_against_the_oracle_golden():
+    """The 4x8 Heisenberg workload (S^z = 0, 601,080,390 states) at full size:
+    20 Lanczos steps from the seeded start vector of the benchmark (seed 2)
+    against the oracle's FP64 run of the same 20 steps
+    (tests/golden/lanczos_square4x8_20steps.json, written by
+    tests/golden/make_lanczos_golden.py, which calls only the oracle): FP64
+    alpha and beta to 1e-10, the lowest Ritz value to 1e-11 relative; the FP32
+    storage run's Ritz value error stated and below 1e-6."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lanczos_square4x8_20steps.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle golden not written yet (tests/golden/make_lanczos_golden.py square4x8)")
+    gold = json.load(open(path))
+    cfg = configs.heisenberg_square4x8()
+    m, b, h = pair(cfg["model"], cfg["n_sites"], cfg["n_up"], cfg["n_dn"], cfg["terms"])
+    assert b.dim == gold["dim"] and gold["seed"] == cfg["seed"] and gold["steps"] == 20
+    v0 = torch.empty(b.dim, dtype=torch.float64, device="cuda")
+    hphi.hphi_random_vector(h.ctx, v0, cfg["seed"])
+    r64 = hphi.hphi_lanczos(h, v0, 20, 0.0, check_every=20)
+    assert r64["steps"] == 20
+    assert np.allclose(r64["alpha"][:20], gold["alpha"], rtol=1e-10, atol=0)
+    # the binding returns beta_1 .. beta_m; the oracle beta_0 (= 0) .. beta_m
+    assert np.allclose(r64["beta"][:20], gold["beta"][1:21], rtol=1e-10, atol=0)
+    e0 = gold["e0"]
+    assert abs(r64["e0"] - e0) <= 1e-11 * abs(e0), (r64["e0"], e0)
+    r32 = hphi.hphi_lanczos(h, v0.float(), 20, 0.0, check_every=20)
+    err = abs(r32["e0"] - e0) / abs(e0)
+    print(f"4x8 FP32 storage, 20 steps: Ritz value error {err:.2e} against the oracle")
+    assert err < 1e-6
