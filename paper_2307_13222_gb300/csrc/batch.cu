@@ -428,12 +428,9 @@ size_t batch_fill(const hphi_ham *h, BProb &P) {
 }
 
 int batch_launch_steps(hphi_ctx *ctx, const BProb *dprob, int n, size_t dyn) {
-    static bool attr[64] = {false};
-    if (!attr[ctx->device]) {
-        HPHI_CUDA(ctx, cudaFuncSetAttribute(k_lzb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-        HPHI_CUDA(ctx, cudaFuncSetAttribute(k_gsb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-        attr[ctx->device] = true;
-    }
+    // the dynamic shared-memory limits of both kernels, raised once per device under a lock
+    if (dyn_occupancy(ctx, (const void *)k_lzb, kBT, dyn) < 1 || dyn_occupancy(ctx, (const void *)k_gsb, kBT, dyn) < 1)
+        return set_err(ctx, HPHI_E_INVAL, "batched Lanczos: %zu bytes of shared memory per problem do not fit", dyn);
     if (n <= 0) return HPHI_OK;
     const int slot = prof_begin(ctx, PROF_HV);
     k_lzb<<<n, kBT, dyn, ctx->stream>>>(dprob);

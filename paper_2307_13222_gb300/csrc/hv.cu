@@ -230,15 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_hv(const HvArgs<T> a) {
 
 template <typename T, int G, int CPL>
 int grid_for(hphi_ctx *ctx, int64_t nh, bool red) {
-    static int occ[64] = {0};
-    int dev = ctx->device;
-    if (occ[dev] == 0) {
-        int n = 0;
-        size_t dyn = 3 * (kThreads / 32) * G * CPL * sizeof(double);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hv<T, G, CPL>, kThreads, dyn);
-        occ[dev] = n > 0 ? n : 1;
-    }
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count;
+    const size_t dyn = 3 * (kThreads / 32) * G * CPL * sizeof(double);
+    const int occ = dyn_occupancy(ctx, (const void *)k_hv<T, G, CPL>, kThreads, dyn);
+    int64_t g = (int64_t)(occ > 0 ? occ : 1) * ctx->sm_count;
     if (g > nh) g = nh;
     if (g < 1) g = 1;
     (void)red;

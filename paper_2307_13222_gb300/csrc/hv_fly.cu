@@ -488,16 +488,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_hvc(const HvArgs<T> a) {
 
 template <typename T, int CPL, int G, int RED, int KB, int MINB>
 int go_c(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int *grid_out) {
-    static int occ[64] = {0};
-    const int dev = ctx->device;
     const size_t dyn = RED ? 3 * (kThreads / 32) * G * CPL * sizeof(double) : 0;
-    if (occ[dev] == 0) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvc<T, CPL, G, RED, KB, MINB>, kThreads, dyn);
-        occ[dev] = n > 0 ? n : 1;
-    }
+    const int occ = dyn_occupancy(ctx, (const void *)k_hvc<T, CPL, G, RED, KB, MINB>, kThreads, dyn);
     const int split = a.P.split;
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count / split;
+    int64_t g = (int64_t)(occ > 0 ? occ : 1) * ctx->sm_count / split;
     if (g > ham->nh) g = ham->nh;
     if (g < 1) g = 1;
     g *= split;
@@ -534,16 +528,10 @@ int go_coop(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int form, in
 
 template <typename T, int CPL, int G, int RED>
 int go(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int *grid_out) {
-    static int occ[64] = {0};
-    const int dev = ctx->device;
     const size_t dyn = RED ? 3 * (kThreads / 32) * G * CPL * sizeof(double) : 0;
-    if (occ[dev] == 0) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvo<T, CPL, G, RED>, kThreads, dyn);
-        occ[dev] = n > 0 ? n : 1;
-    }
+    const int occ = dyn_occupancy(ctx, (const void *)k_hvo<T, CPL, G, RED>, kThreads, dyn);
     const int split = a.P.split;
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count / split;
+    int64_t g = (int64_t)(occ > 0 ? occ : 1) * ctx->sm_count / split;
     if (g > ham->nh) g = ham->nh;
     if (g < 1) g = 1;
     g *= split;

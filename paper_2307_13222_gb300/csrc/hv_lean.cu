@@ -324,17 +324,11 @@ __global__ void __launch_bounds__(kThreads, (CPL >= 4 || sizeof(T) == 8) ? 2 : 3
 
 template <typename T, int CPL, int LDC, int RED>
 int go(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int *grid_out) {
-    static int occ[64] = {0};
-    const int dev = ctx->device;
     const size_t dyn = RED ? 3 * (kThreads / 32) * CPL * sizeof(double) : 0;
-    if (occ[dev] == 0) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hvl<T, CPL, LDC, RED>, kThreads, dyn);
-        occ[dev] = n > 0 ? n : 1;
-    }
+    const int occ = dyn_occupancy(ctx, (const void *)k_hvl<T, CPL, LDC, RED>, kThreads, dyn);
     // a multiple of the split: `split` consecutive thread blocks share a row block
     const int split = a.P.split;
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count / split;
+    int64_t g = (int64_t)(occ > 0 ? occ : 1) * ctx->sm_count / split;
     if (g > ham->nh) g = ham->nh;
     if (g < 1) g = 1;
     g *= split;

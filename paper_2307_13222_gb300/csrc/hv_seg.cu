@@ -181,15 +181,9 @@ int launch_seg(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, int red_mode, i
     const double per_l1 = (double)ham->D * sizeof(T) / (double)(1u << s.n1);
     int wbits = 0;
     while (wbits < s.n1 && per_l1 * (double)(2u << wbits) <= 0.3 * (double)l2) wbits++;
-    static int occ[64] = {0};
-    const int dev = ctx->device;
-    if (occ[dev] == 0) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hhs<T>, 32 * kHhsWarps, 0);
-        occ[dev] = n > 0 ? n : 1;
-    }
+    const int occ = dyn_occupancy(ctx, (const void *)k_hhs<T>, 32 * kHhsWarps, 0);
     const int64_t units = ((int64_t)1 << s.nhi) << (s.n1 - wbits);
-    int64_t g = (int64_t)occ[dev] * ctx->sm_count;
+    int64_t g = (int64_t)(occ > 0 ? occ : 1) * ctx->sm_count;
     const int64_t need_blocks = (units + kHhsWarps - 1) / kHhsWarps;
     if (g > need_blocks) g = need_blocks;
     if (g < 1) g = 1;

@@ -382,28 +382,18 @@ int launch_tile(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<float> &a, int red_mo
         }
         tbuf = (float *)ctx->seg_tmp;
     }
-    static int occ1[64] = {0}, occ2[64][4] = {{0}};
-    const int dev = ctx->device;
-    if (occ1[dev] == 0) {
-        auto occ_of = [](const void *f) {
-            int n = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kTileThreads, 0);
-            return n > 0 ? n : 1;
-        };
-        occ1[dev] = occ_of((const void *)k_tile<1, 0>);
-        occ2[dev][0] = occ_of((const void *)k_tile<2, 0>);
-        occ2[dev][1] = occ_of((const void *)k_tile<2, 1>);
-        occ2[dev][2] = occ_of((const void *)k_tile<2, 2>);
-        occ2[dev][3] = occ_of((const void *)k_tile<2, 3>);
-    }
     if (red_mode < 0 || red_mode > 3) return set_err(ctx, HPHI_E_INVAL, "tiled H*V: unknown reduction mode");
+    static const void *const pass2[4] = {(const void *)k_tile<2, 0>, (const void *)k_tile<2, 1>,
+                                         (const void *)k_tile<2, 2>, (const void *)k_tile<2, 3>};
     // no more thread blocks than the partials of an H*x launch hold (8 per SM)
-    auto grid_of = [&](int occ) {
-        int64_t g = (int64_t)(occ < 8 ? occ : 8) * ctx->sm_count;
+    auto grid_of = [&](const void *f) {
+        int occ = dyn_occupancy(ctx, f, kTileThreads, 0);
+        occ = occ < 1 ? 1 : (occ < 8 ? occ : 8);
+        int64_t g = (int64_t)occ * ctx->sm_count;
         if (g > ham->nh) g = ham->nh;
         return (int)(g < 1 ? 1 : g);
     };
-    const int g1 = grid_of(occ1[dev]), g2 = grid_of(occ2[dev][red_mode]);
+    const int g1 = grid_of((const void *)k_tile<1, 0>), g2 = grid_of(pass2[red_mode]);
     *grid = g2;
     const int slot = prof_begin(ctx, PROF_HV);
     int st = go_tile<1>(ctx, a, ta, ham->tile_diag, tbuf, 0, g1);
