@@ -828,7 +828,7 @@ def run_ctpq26(args):
     es = 8 if tdt == torch.complex64 else 16
     # algorithmic bytes of one Horner stage: read V + gather W + write W' per complex column
     stage_bytes = 3.0 * es * cfg["n_vec"] * b.dim
-    roof = _roofline(ctx, stage_bytes, "k_hvc / k_hvo (block H*V, 32 real columns)")
+    roof = _roofline(ctx, stage_bytes, ctx.last_kernel())
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O

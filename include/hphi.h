@@ -178,7 +178,7 @@ HPHI_API int64_t hphi_ham_dim(const hphi_ham *ham);
  *                         high-high bonds over L2-sized chunks of the low
  *                         half, then the bond-major kernel without them
  *                         (same shapes as 3, D < 2^31; on request), 5 =
- *                         tiled: full space, 32 FP32 columns, the bonds split
+ *                         tiled: full space, 32 columns (FP32 or FP64), the bonds split
  *                         over two passes that each gather only inside an
  *                         L2-resident tile of rows (automatic there when the
  *                         bond graph has such a split)

@@ -144,9 +144,11 @@ void free_ham(hphi_ham *h) {
     cudaFree(h->dterms_d);
     cudaFree(h->rowstate);
     cudaFree(h->seg_so);
-    cudaFree(h->tile_tab);
-    cudaFree(h->tile_diag);
-    delete h->tile;
+    for (int p = 0; p < 2; p++) {
+        cudaFree(h->tile_tab[p]);
+        cudaFree(h->tile_diag[p]);
+        delete h->tile[p];
+    }
     delete h->seg;
     delete h;
 }

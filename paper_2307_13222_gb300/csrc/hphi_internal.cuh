@@ -199,11 +199,12 @@ struct hphi_ham {
     // arguments (null when not available) and its device table
     hphi::SegArgs *seg = nullptr;
     uint16_t *seg_so = nullptr;
-    // tiled block kernel (full space, 32 FP32 columns): built on first use
-    hphi::TileArgs *tile = nullptr;
-    int tile_tried = 0;
-    uint32_t *tile_tab = nullptr;
-    float *tile_diag = nullptr;  // the diagonal of H, one FP32 value per row
+    // tiled block kernel (full space, 32 columns), per precision [0: FP32, 1: FP64]
+    // (the tiles follow the row size): built on first use
+    hphi::TileArgs *tile[2] = {nullptr, nullptr};
+    int tile_tried[2] = {0, 0};
+    uint32_t *tile_tab[2] = {nullptr, nullptr};
+    void *tile_diag[2] = {nullptr, nullptr};  // the diagonal of H, one value per row in that precision
     // plain term list (host and device) and, for the S^z sector, the state of
     // every row (built on first use by the small-problem solver)
     std::vector<hphi::DTerm> dterms;
@@ -324,7 +325,7 @@ int lowest_ritz_warm(int m, const double *alpha, const double *beta2, double *wa
 // ---- high-high pass table (hv_seg.cu) ------------------------------------------------
 int build_seg_tables(hphi_ctx *ctx, hphi_ham *H);
 // ---- tiled block kernel tables (hv_tile.cu) ------------------------------------------
-int build_tile_tables(hphi_ctx *ctx, hphi_ham *H);
+int build_tile_tables(hphi_ctx *ctx, hphi_ham *H, int prec);
 
 // ---- pattern (pattern.cu) --------------------------------------------------------
 int dump_rows(hphi_ctx *ctx, const hphi_ham *ham, int64_t row0, int64_t row1, std::vector<int64_t> &cols,

@@ -376,17 +376,18 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
         if (L.swap && ((nc % 2) != 0 || (c0 % 2) != 0 || (fG == 1 && fcpl == 1) || (cpl == 1)))
             return set_err(ctx, HPHI_E_INVAL, "pair swap: column slice [%d, %d) splits a pair", c0, c0 + nc);
         int grid = 0, st;
-        // the tiled two-pass block kernel (variant 5, automatic there): full space, 32 FP32
-        // columns, 16-byte rows (measured 1.3x faster than the single-pass kernels on the
-        // N=26 cTPQ block)
+        // the tiled two-pass block kernel (variant 5, automatic there): full space, 32
+        // columns, 16-byte accesses (measured on the N=26 cTPQ block: 1.3x faster than the
+        // single-pass kernels in FP32, 1.1x in FP64)
         bool tiled = false;
-        if constexpr (std::is_same<T, float>::value) {
+        {
+            constexpr int prec = std::is_same<T, float>::value ? 0 : 1;
             if ((ham->tune_variant == 5 || ham->tune_variant < 0) && ham->model == HPHI_SPIN_HALF_GC && c0 == 0 &&
                 L.ncol == 32 &&
                 L.ldx == 32 && L.ldy == 32 && (!L.v || L.ldv == 32) && red_mode >= 0 && aligned(xs, 16) &&
                 aligned(ys, 16) && aligned(vs, 16)) {
-                if ((st = build_tile_tables(ctx, const_cast<hphi_ham *>(ham)))) return st;
-                tiled = ham->tile != nullptr;
+                if ((st = build_tile_tables(ctx, const_cast<hphi_ham *>(ham), prec))) return st;
+                tiled = ham->tile[prec] != nullptr;
             }
         }
         if (tiled) {
@@ -395,7 +396,7 @@ int launch_typed(hphi_ctx *ctx, const hphi_ham *ham, HvLaunch &L) {
                 a.alpha[c] = L.alpha_h ? L.alpha_h[c] : L.alpha_s;
                 a.gamma[c] = L.gamma_h ? L.gamma_h[c] : L.gamma_s;
             }
-            if constexpr (std::is_same<T, float>::value) st = launch_tile(ctx, ham, a, red_mode, &grid);
+            st = launch_tile<T>(ctx, ham, a, red_mode, &grid);
             if (st) return st;
             L.sgrid[L.nslice] = grid;
             L.sc0[L.nslice] = 0;

@@ -221,8 +221,9 @@ int launch_staged(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int re
 template <typename T>
 int launch_phased(hphi_ctx *ctx, const hphi_ham *ham, const HvArgs<T> &a, int red_mode, int *grid);
 uint32_t staged_block_len(const hphi_ham *ham);
-// tiled two-pass block kernel (hv_tile.cu): full space, 32 FP32 columns
-int launch_tile(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<float> &a, int red_mode, int *grid);
+// tiled two-pass block kernel (hv_tile.cu): full space, 32 columns (FP32 or FP64)
+template <typename T>
+int launch_tile(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, int red_mode, int *grid);
 // high-high pass plus the bond-major kernel (hv_seg.cu): spin sector, one column
 template <typename T>
 int launch_seg(hphi_ctx *ctx, const hphi_ham *ham, HvArgs<T> &a, int red_mode, int *grid);

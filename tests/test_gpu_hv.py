@@ -377,27 +377,30 @@ def test_fused_reductions_one_column_sector(variant):
         assert np.allclose(logd, np.log(do), rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("N,seed", [(12, 9), (20, 3), (22, 4)])
-def test_tiled_block_kernel(N, seed):
+def test_tiled_block_kernel(N, seed, dtype):
     """Tiled two-pass block kernel (variant 5; full space, 32 FP32 columns):
     one tile holding every row (N = 12) and two passes over tiles of the
     bond-graph split (N = 20, 22), plain and with the accumulate term."""
     bonds = random_regular_graph(N, 3, seed)
     m, b, h = pair("SPIN_HALF_GC", N, 0, 0, heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, seed + 7)))
     h.set_tuning(variant=5)
-    _check(m, h, torch.float32, 32, alpha=1.1, beta=0.0, seed=30 + N)
-    assert h.ctx.last_kernel().startswith("k_tile<f32,"), h.ctx.last_kernel()
-    _check(m, h, torch.float32, 32, alpha=-0.6, beta=0.25, seed=31 + N)
+    _check(m, h, dtype, 32, alpha=1.1, beta=0.0, seed=30 + N)
+    want = "k_tile<f32," if dtype == torch.float32 else "k_tile<f64,"
+    assert h.ctx.last_kernel().startswith(want), h.ctx.last_kernel()
+    _check(m, h, dtype, 32, alpha=-0.6, beta=0.25, seed=31 + N)
 
 
-def test_tiled_block_rrg26_full_size_sampled():
-    """The cTPQ block shape at full size (2^26 rows x 16 complex FP32 columns)
-    through the tiled kernel: two passes with 2^18- and 2^15-row tiles."""
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_tiled_block_rrg26_full_size_sampled(dtype):
+    """The cTPQ block shape at full size (2^26 rows x 16 complex columns, FP32
+    and FP64) through the tiled kernel: two passes over L2-sized tiles."""
     bonds = random_regular_graph(26, 3, 4)
     terms = heisenberg_terms(bonds, uniform_couplings(len(bonds), 0.5, 1.5, 1004))
     m, b, h = pair("SPIN_HALF_GC", 26, 0, 0, terms)
     h.set_tuning(variant=5)
     rng = np.random.default_rng(11)
     rows = np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, 200)])
-    assert _sampled_rows(m, h, torch.float32, 32, rows, 45) < 1e-6
-    assert h.ctx.last_kernel().startswith("k_tile<f32,")
+    assert _sampled_rows(m, h, dtype, 32, rows, 45) < (1e-6 if dtype == torch.float32 else 1e-14)
+    assert h.ctx.last_kernel().startswith("k_tile<f32," if dtype == torch.float32 else "k_tile<f64,")

@@ -54,7 +54,7 @@ def test_tpq_sector_model():
 def test_tpq_block_of_16_complex_vectors(coop, dtype):
     """16 complex vectors = 32-column rows, the fused <x,Hx>, |Hx|^2, |x|^2
     reductions of the wide-row kernel in both bond-sharing modes, and of the
-    tiled two-pass kernel (FP32 data; FP64 keeps the wide-row kernel)."""
+    tiled two-pass kernel (FP32 and FP64 data)."""
     m, b, h = pair("SPIN_HALF_GC", 12, 0, 0, _model(12, 5))
     if coop == "tiled":
         h.set_tuning(variant=5)
